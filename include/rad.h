@@ -1,0 +1,184 @@
+/*
+ * rad.h -- C ABI of the GB300 in-situ radiation-spectrum accumulator.
+ *
+ * The library computes, for every tracked particle j, observer direction n
+ * and frequency omega, the Lienard-Wiechert far-field spectrum accumulated
+ * over the PIC time steps, and sums it over particles (Frederiksen et al.,
+ * "Radiation Spectral Synthesis of Relativistic Filamentation", Sec. 2.2:
+ * the discretised integral P_omega ~ |int sum_j E_ret,j exp(i omega phi') dt'|^2
+ * with phi' = t' - n.r(t')/c, multiple far-field observers at arbitrary
+ * orientation, logarithmic or linear frequency bins, phase-coherent or
+ * phase-incoherent synthesis, spectra recorded over windows of steps).  The
+ * integrand is the Jackson retarded-time form the paper cites through
+ * Rybicki & Lightman:
+ *
+ *   d^2W/(dw dOmega) = q^2/(4 pi^2 c) |sum_m n x ((n-beta) x betadot)/(1-n.beta)^2
+ *                                        exp(i w (t_m - n.r_m/c)) dt|^2
+ *
+ * Units follow the paper's PIC scaling (Sec. 2.1): c = 1, time in 1/omega_pe,
+ * frequencies in omega_pe; u = gamma*beta is the momentum per unit mass.
+ *
+ * Call protocol (leapfrog, the reading of Sec. 2.2's time integral): the call
+ * for step s passes x_s (position at t = s dt, possibly wrapped into a
+ * periodic box) and u_{s-1/2}.  Sample m uses r_m (unwrapped x_m),
+ * beta_m = ubar/sqrt(1+ubar^2) with ubar = (u_{m-1/2}+u_{m+1/2})/2 and
+ * betadot_m = (beta_{m+1/2} - beta_{m-1/2})/dt, so sample m is complete after
+ * the call for step m+1.  A window [s0, s1) of samples therefore closes after
+ * the call for step s1.  Steps start at 0 and increase by one.
+ *
+ * Memory: every pointer argument may point to host memory (pageable or
+ * pinned) or device memory of the context's device; the library detects which
+ * and copies what it needs.  The caller keeps ownership of everything it
+ * passes.  Device-resident inputs are read on the context's stream, so the
+ * caller may reuse them once work enqueued on that stream after the call has
+ * completed.  Host-resident inputs may be reused as soon as the call returns.
+ *
+ * Errors: every int-returning call returns RAD_OK (0) or a negative RAD_E*
+ * code; rad_last_error() gives a one-line description.  A failed call leaves
+ * the context usable unless it returns RAD_ECUDA.
+ */
+#ifndef RAD_H
+#define RAD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RAD_OK 0
+#define RAD_EINVAL (-1)      /* bad argument */
+#define RAD_ENOMEM (-2)      /* device or host allocation failed */
+#define RAD_ECUDA (-3)       /* a CUDA call failed; see rad_last_error */
+#define RAD_ESTEP (-4)       /* step is not previous step + 1 (first must be 0) */
+#define RAD_EINCOMPLETE (-5) /* finalize before every window's last sample arrived */
+#define RAD_ETIMEOUT (-6)    /* a bounded device-side wait expired; results invalid */
+#define RAD_ENAN (-7)        /* non-finite input detected (check_inputs option) */
+#define RAD_ESTATE (-8)      /* call not allowed in the context's current state */
+
+/* summation over particles (Sec. 2.2: "phase coherent or phase incoherent") */
+#define RAD_INCOHERENT 0     /* S = 1/(4 pi^2) sum_j |q_j A_j|^2 */
+#define RAD_COHERENT 1       /* S = 1/(4 pi^2) |sum_j q_j A_j|^2 */
+
+/* arithmetic of the accumulation */
+#define RAD_FP64 0           /* FP64 geometry, phase and sums; CUDA double sincos */
+#define RAD_FP32_SPLIT 1     /* FP32 bulk; FP64 retarded-time anchor every K samples */
+
+/* sincos engine of the FP32 split path */
+#define RAD_VARIANT_AUTO 0   /* autotuned (or the cached choice) */
+#define RAD_VARIANT_SFU 1    /* every e^{i theta} by the special-function unit */
+#define RAD_VARIANT_MIX 2    /* part of the frequencies by an FMA-pipe polynomial */
+
+typedef struct rad_ctx rad_ctx;
+
+/* One particle species: `count` consecutive particles of the particle axis. */
+typedef struct {
+    int64_t count;   /* particles of this species (>= 0) */
+    double charge;   /* q in units of the elementary charge (electron: -1) */
+    double mass;     /* m in electron masses; informational (u is per unit mass) */
+} rad_species;
+
+/* One spectrum window: samples [s0, s1) of the species in species_mask (bit i
+ * = species i), on frequency grid freq_grid.  The output holds, per window,
+ * a [D][len(grid)] block (Sec. 2.2: spectra "recorded every small multiple of
+ * a simulation timestep"; a cumulative snapshot is the window [0, t)). */
+typedef struct {
+    int64_t s0, s1;
+    uint32_t species_mask;
+    int32_t freq_grid;
+} rad_window;
+
+/* Tuning knobs; zero-initialise for the defaults.  Set before the first step. */
+typedef struct {
+    int32_t variant;       /* RAD_VARIANT_*                                  */
+    int32_t anchor_K;      /* FP32 path re-anchor interval: 0 (auto), 8, 16, 32 */
+    int32_t freq_per_lane; /* 0 (auto), 8 or 16 frequencies per thread         */
+    int32_t defer;         /* 1: evaluate every window in one persistent launch at
+                              finalize instead of when its last sample arrives */
+    int32_t use_graph;     /* 1: replay each step's work as a CUDA graph        */
+    int32_t check_inputs;  /* 1: flag non-finite x/u (RAD_ENAN at finalize)    */
+    int32_t mix_sfu_of_16; /* MIX variant: frequencies (of every 16) on the SFU */
+    int32_t reserved[9];
+} rad_options;
+
+/*
+ * rad_init -- create a context (Sec. 2.2: observers, frequency bins, tracked
+ * particles, coherent/incoherent choice).
+ *   out        : receives the context.
+ *   dirs       : [D][3] observer directions (normalised by the library), D >= 1.
+ *   freqs      : concatenation of n_grids frequency grids (any spacing; > 0
+ *                not required), grid g has grid_len[g] >= 1 points.
+ *   dt         : time step (> 0).
+ *   sp         : n_species >= 1 species; particle axis = species concatenated.
+ *   win        : n_win >= 1 windows, 0 <= s0 <= s1, grid index in range,
+ *                species_mask within the species.
+ *   mode       : RAD_INCOHERENT or RAD_COHERENT.
+ *   precision  : RAD_FP64 or RAD_FP32_SPLIT.
+ *   box_L      : periodic box side for unwrapping positions (0: no unwrap).
+ *   cuda_stream: cudaStream_t to enqueue on (NULL: the legacy default stream).
+ * Allocates all device memory the context needs (trajectory ring, state,
+ * accumulators); returns RAD_ENOMEM if it does not fit.  On error *out is NULL.
+ */
+int rad_init(rad_ctx **out, const double *dirs, int32_t D, const double *freqs,
+             const int32_t *grid_len, int32_t n_grids, double dt, const rad_species *sp,
+             int32_t n_species, const rad_window *win, int32_t n_win, int32_t mode,
+             int32_t precision, double box_L, void *cuda_stream);
+
+/* rad_set_options -- set tuning knobs; RAD_ESTATE after the first step. */
+int rad_set_options(rad_ctx *ctx, const rad_options *opt);
+
+/* rad_get_options -- the knobs in effect (after autotuning if it ran). */
+int rad_get_options(const rad_ctx *ctx, rad_options *opt);
+
+/*
+ * rad_accumulate -- hand over one PIC step (Sec. 2.2: spectra are collected
+ * at runtime).  x and u are SoA [3][N_total] FP64 (x: x_step, u: u_{step-1/2}).
+ * Windows whose last sample completes with this step are evaluated now
+ * (unless the defer option is set).  Returns before the device work is done.
+ */
+int rad_accumulate(rad_ctx *ctx, int64_t step, const double *x, const double *u);
+
+/*
+ * rad_accumulate_steps -- hand over n_steps consecutive steps at once:
+ * x, u are [n_steps][3][N_total] FP64.  Equivalent to n_steps calls of
+ * rad_accumulate, with fewer launches.
+ */
+int rad_accumulate_steps(rad_ctx *ctx, int64_t step0, int64_t n_steps, const double *x,
+                         const double *u);
+
+/*
+ * rad_finalize -- evaluate deferred windows, scale by 1/(4 pi^2 c) and write
+ * the spectra: spectrum is [n_win][D][len(grid of window)] FP64 concatenated
+ * over windows (host or device).  Synchronises the context's stream.  Returns
+ * RAD_EINCOMPLETE if a window's last sample has not arrived, RAD_ETIMEOUT or
+ * RAD_ENAN if a device-side check failed.  May be called more than once.
+ */
+int rad_finalize(rad_ctx *ctx, double *spectrum);
+
+/* rad_reset -- forget all steps and zero the accumulators (same configuration). */
+int rad_reset(rad_ctx *ctx);
+
+/* rad_spectrum_size -- number of doubles rad_finalize writes (or -1). */
+int64_t rad_spectrum_size(const rad_ctx *ctx);
+
+/* rad_updates -- particle*sample*omega*direction updates over all windows. */
+int64_t rad_updates(const rad_ctx *ctx);
+
+/*
+ * rad_timing -- device time (CUDA events on the context's stream) spent since
+ * init/reset in the window accumulation kernels and in the per-step ingest,
+ * and the number of accumulation launches.  Synchronises the stream.
+ */
+int rad_timing(rad_ctx *ctx, double *accum_ms, double *ingest_ms, int64_t *accum_launches,
+               int64_t *ingest_launches);
+
+/* rad_last_error -- description of the last failure on ctx (never NULL). */
+const char *rad_last_error(const rad_ctx *ctx);
+
+/* rad_destroy -- free the context (NULL is allowed). */
+void rad_destroy(rad_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RAD_H */

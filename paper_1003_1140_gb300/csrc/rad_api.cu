@@ -1,0 +1,815 @@
+// rad_api.cu -- host side of the C ABI declared in include/rad.h.
+//
+// Owns the context: observer basis, frequency tables, species/column map,
+// the trajectory ring and per-particle leapfrog state, the FP64 spectrum
+// accumulators, the per-event work lists and the TMA descriptors.  Every
+// arithmetic step of the diagnostic runs in the kernels of rad_ingest.cu,
+// rad_accum32.cu, rad_accum64.cu and the finalize kernel below.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include <cudaTypedefs.h>
+
+#include "rad.h"
+#include "rad_internal.cuh"
+
+using namespace rad;
+
+struct Event {
+    int64_t call;                 // step after which the windows close
+    std::vector<int> wins;
+    std::vector<WorkItem> items;  // host copy
+    WorkItem* d_items = nullptr;
+};
+
+struct rad_ctx {
+    // configuration
+    int D = 0;
+    int n_grids = 0;
+    std::vector<int> grid_off, grid_len;
+    double dt = 0.0, box_L = 0.0;
+    int mode = 0, precision = 0;
+    int n_species = 0;
+    std::vector<rad_species> species;
+    std::vector<int64_t> in_off;   // [n_species + 1]
+    std::vector<int32_t> col_off;  // [n_species]
+    int64_t n_in = 0, ncols = 0;
+    std::vector<rad_window> wins;
+    std::vector<int64_t> out_off;
+    int64_t out_len = 0;
+    rad_options opt{};
+    int ft = 16, K = 16;
+    bool frozen = false;           // options frozen after the first step
+
+    // device / stream
+    int device = 0;
+    int sms = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t copy_stream = nullptr;
+
+    // ring
+    int64_t ring = 0, nblk = 0;
+    float* slab32 = nullptr;
+    double* slab64 = nullptr;
+    double* anchors = nullptr;
+    double* x_prev = nullptr;
+    double* r_prev = nullptr;
+    double* u_prev = nullptr;
+    CUtensorMap tmap{};
+
+    // tables
+    float* d_dirs32 = nullptr;
+    double* d_dirs64n = nullptr;   // [D][3] n (FP32 path phase)
+    double* d_dirs64 = nullptr;    // [D][9] n, e1, e2
+    float* d_om32 = nullptr;
+    float* d_nuhi = nullptr;
+    float* d_nulo = nullptr;
+    double* d_om64 = nullptr;
+    WinDev* d_wins = nullptr;
+    SpeciesDev* d_species = nullptr;
+
+    // accumulators
+    double* acc = nullptr;       // [out_len] or [out_len][4]
+    double* d_out = nullptr;     // scaled spectrum staging (device)
+    int* d_err = nullptr;
+
+    // staging for host inputs
+    double* stage[2] = {nullptr, nullptr};
+    int64_t stage_steps = 0;
+    cudaEvent_t copy_done[2] = {nullptr, nullptr};
+    cudaEvent_t used_done[2] = {nullptr, nullptr};
+    int stage_next = 0;
+
+    // events of the step axis
+    std::vector<Event> events;     // eager: sorted by call; defer: one event
+    std::map<int64_t, int> event_at;
+    int64_t next_step = 0;
+    int64_t max_s1 = 0;
+    bool deferred_done = false;     // deferred windows already evaluated
+
+    // timing
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> acc_ev, ing_ev;
+    size_t acc_used = 0, ing_used = 0;
+    int64_t acc_launches = 0, ing_launches = 0;
+    bool time_ingest = false;
+
+    std::string err;
+};
+
+static const char* kNoCtx = "null context";
+
+static int fail(rad_ctx* c, int code, const char* fmt, ...)
+{
+    if (!c) return code;
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    c->err = buf;
+    return code;
+}
+
+#define CU(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(c, e_ == cudaErrorMemoryAllocation ? RAD_ENOMEM : RAD_ECUDA,    \
+                        "%s failed: %s", #call, cudaGetErrorString(e_));                \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// finalize kernel: S = acc / (4 pi^2 c) (incoherent) or |sum A|^2 / (4 pi^2 c)
+// ---------------------------------------------------------------------------
+__global__ void finalize_kernel(const double* acc, double* out, int64_t n, int coherent)
+{
+    const double pref = 1.0 / (4.0 * 3.14159265358979323846 * 3.14159265358979323846);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (coherent) {
+            const double* a = acc + 4 * i;
+            out[i] = pref * (a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
+        } else {
+            out[i] = pref * acc[i];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+static bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static void basis(const double n[3], double e1[3], double e2[3])
+{
+    // e1 = normalise(n x a), a = the coordinate axis least aligned with n
+    double ax[3] = {0, 0, 0};
+    int k = 0;
+    for (int i = 1; i < 3; ++i)
+        if (std::fabs(n[i]) < std::fabs(n[k])) k = i;
+    ax[k] = 1.0;
+    double c[3] = {n[1] * ax[2] - n[2] * ax[1], n[2] * ax[0] - n[0] * ax[2],
+                   n[0] * ax[1] - n[1] * ax[0]};
+    double l = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    for (int i = 0; i < 3; ++i) e1[i] = c[i] / l;
+    e2[0] = n[1] * e1[2] - n[2] * e1[1];
+    e2[1] = n[2] * e1[0] - n[0] * e1[2];
+    e2[2] = n[0] * e1[1] - n[1] * e1[0];
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+static int chunk_len(const rad_ctx* c) { return c->precision == RAD_FP64 ? kChunk64 : kChunk32; }
+
+static int freq_tile(const rad_ctx* c)
+{
+    return c->precision == RAD_FP64 ? 32 * accum64_ft() : 32 * c->ft;
+}
+
+// Build the work items of one event (set of windows) and sort by cost.
+static void build_items(rad_ctx* c, Event& ev, int total_blocks)
+{
+    const int ftl = freq_tile(c);
+    const int ch = chunk_len(c);
+    // total (tile x direction x ftile) units, to size the particle groups
+    double units = 0;
+    for (int w : ev.wins) {
+        const rad_window& W = c->wins[w];
+        const int nft = (c->grid_len[W.freq_grid] + ftl - 1) / ftl;
+        for (int s = 0; s < c->n_species; ++s)
+            if ((W.species_mask >> s) & 1u)
+                units += (double)((c->species[s].count + kTileP - 1) / kTileP) * nft * c->D;
+    }
+    const double target_items = 8.0 * std::max(1, total_blocks);
+    int G = (int)std::max(1.0, std::floor(units / target_items));
+    ev.items.clear();
+    std::vector<int64_t> cost;
+    for (int w : ev.wins) {
+        const rad_window& W = c->wins[w];
+        if (W.s1 <= W.s0) continue;
+        const int nft = (c->grid_len[W.freq_grid] + ftl - 1) / ftl;
+        const int64_t nch = (W.s1 - 1) / ch - W.s0 / ch + 1;
+        for (int s = 0; s < c->n_species; ++s) {
+            if (!((W.species_mask >> s) & 1u) || c->species[s].count == 0) continue;
+            const int nt = (int)((c->species[s].count + kTileP - 1) / kTileP);
+            for (int d = 0; d < c->D; ++d)
+                for (int f = 0; f < nft; ++f)
+                    for (int t0 = 0; t0 < nt; t0 += G) {
+                        WorkItem it{w, d, f, s, t0, std::min(G, nt - t0)};
+                        ev.items.push_back(it);
+                        cost.push_back((int64_t)it.ntiles * nch);
+                    }
+        }
+    }
+    std::vector<size_t> ord(ev.items.size());
+    for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+    std::vector<WorkItem> sorted(ord.size());
+    for (size_t i = 0; i < ord.size(); ++i) sorted[i] = ev.items[ord[i]];
+    ev.items.swap(sorted);
+}
+
+static int blocks_per_sm(const rad_ctx* c)
+{
+    if (c->precision == RAD_FP64) return std::max(1, accum64_blocks_per_sm(c->mode == RAD_COHERENT));
+    return std::max(1, accum32_blocks_per_sm(c->ft, c->K, c->mode == RAD_COHERENT));
+}
+
+static cudaEvent_t next_event(std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& pool, size_t& used,
+                              bool start)
+{
+    if (start) {
+        if (used == pool.size()) {
+            cudaEvent_t a, b;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            pool.push_back({a, b});
+        }
+        return pool[used].first;
+    }
+    return pool[used++].second;
+}
+
+// Freeze options: pick K / FT, build events, item lists, TMA map.
+static int freeze(rad_ctx* c)
+{
+    if (c->frozen) return RAD_OK;
+    CU(cudaSetDevice(c->device));
+    if (c->precision == RAD_FP32_SPLIT) {
+        c->K = c->opt.anchor_K ? c->opt.anchor_K : 16;
+        int maxlen = 1;
+        for (int g = 0; g < c->n_grids; ++g) maxlen = std::max(maxlen, c->grid_len[g]);
+        c->ft = c->opt.freq_per_lane ? c->opt.freq_per_lane : (maxlen <= 256 ? 8 : 16);
+        // anchor positions: one FP64 3-vector per particle per K samples of the ring
+        c->nblk = c->ring / c->K;
+        if (!c->anchors) {
+            CU(cudaMalloc(&c->anchors, (size_t)c->nblk * 3 * c->ncols * sizeof(double)));
+            CU(cudaMemset(c->anchors, 0, (size_t)c->nblk * 3 * c->ncols * sizeof(double)));
+        }
+    }
+    // events
+    c->events.clear();
+    c->event_at.clear();
+    if (c->opt.defer) {
+        Event ev;
+        ev.call = -1;
+        for (size_t w = 0; w < c->wins.size(); ++w) ev.wins.push_back((int)w);
+        c->events.push_back(ev);
+    } else {
+        std::map<int64_t, std::vector<int>> by;
+        for (size_t w = 0; w < c->wins.size(); ++w)
+            if (c->wins[w].s1 > c->wins[w].s0) by[c->wins[w].s1].push_back((int)w);
+        for (auto& kv : by) {
+            Event ev;
+            ev.call = kv.first;
+            ev.wins = kv.second;
+            c->event_at[kv.first] = (int)c->events.size();
+            c->events.push_back(ev);
+        }
+    }
+    const int total_blocks = blocks_per_sm(c) * c->sms;
+    for (auto& ev : c->events) {
+        build_items(c, ev, total_blocks);
+        if (!ev.items.empty()) {
+            CU(cudaMalloc(&ev.d_items, ev.items.size() * sizeof(WorkItem)));
+            CU(cudaMemcpy(ev.d_items, ev.items.data(), ev.items.size() * sizeof(WorkItem),
+                          cudaMemcpyHostToDevice));
+        }
+    }
+    // TMA descriptor over the ring
+    auto enc = get_encode();
+    if (!enc) return fail(c, RAD_ECUDA, "cuTensorMapEncodeTiled is not available");
+    const bool f64 = c->precision == RAD_FP64;
+    const size_t es = f64 ? 8 : 4;
+    cuuint64_t dims[3] = {(cuuint64_t)c->ncols, (cuuint64_t)kComps, (cuuint64_t)c->ring};
+    cuuint64_t strides[2] = {(cuuint64_t)(c->ncols * es), (cuuint64_t)(c->ncols * es * kComps)};
+    cuuint32_t box[3] = {(cuuint32_t)kTileP, (cuuint32_t)kComps, (cuuint32_t)chunk_len(c)};
+    cuuint32_t estr[3] = {1, 1, 1};
+    void* base = f64 ? (void*)c->slab64 : (void*)c->slab32;
+    CUresult r = enc(&c->tmap, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                     3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(c, RAD_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    c->frozen = true;
+    return RAD_OK;
+}
+
+static int launch_event(rad_ctx* c, Event& ev)
+{
+    if (ev.items.empty()) return RAD_OK;
+    const int total_blocks = blocks_per_sm(c) * c->sms;
+    const int grid = (int)std::min<int64_t>((int64_t)ev.items.size(), total_blocks);
+    cudaEvent_t e0 = next_event(c->acc_ev, c->acc_used, true);
+    CU(cudaEventRecord(e0, c->stream));
+    cudaError_t e;
+    if (c->precision == RAD_FP64) {
+        Accum64Params p{};
+        p.items = ev.d_items;
+        p.n_items = (int32_t)ev.items.size();
+        p.wins = c->d_wins;
+        p.species = c->d_species;
+        p.dirs64 = c->d_dirs64;
+        p.omega = c->d_om64;
+        p.ring = c->ring;
+        p.dt = c->dt;
+        p.acc = c->acc;
+        p.err_word = c->d_err;
+        e = launch_accum64(c->tmap, p, c->mode == RAD_COHERENT, grid, c->stream);
+    } else {
+        Accum32Params p{};
+        p.items = ev.d_items;
+        p.n_items = (int32_t)ev.items.size();
+        p.wins = c->d_wins;
+        p.species = c->d_species;
+        p.dirs32 = c->d_dirs32;
+        p.dirs64 = c->d_dirs64n;
+        p.omega = c->d_om32;
+        p.nu_hi = c->d_nuhi;
+        p.nu_lo = c->d_nulo;
+        p.anchors = c->anchors;
+        p.ncols = c->ncols;
+        p.ring = c->ring;
+        p.nblk = c->nblk;
+        p.dt = c->dt;
+        p.acc = c->acc;
+        p.err_word = c->d_err;
+        e = launch_accum32(c->tmap, p, c->ft, c->K, c->mode == RAD_COHERENT, grid, c->stream);
+    }
+    if (e != cudaSuccess) return fail(c, RAD_ECUDA, "accumulation launch failed: %s", cudaGetErrorString(e));
+    cudaEvent_t e1 = next_event(c->acc_ev, c->acc_used, false);
+    CU(cudaEventRecord(e1, c->stream));
+    ++c->acc_launches;
+    return RAD_OK;
+}
+
+// Ingest n steps from device arrays x, u ([n][3][n_in]) starting at step0.
+static int ingest_device(rad_ctx* c, int64_t step0, int64_t n, const double* x, const double* u)
+{
+    IngestParams p{};
+    p.n_in = c->n_in;
+    p.dt = c->dt;
+    p.box_L = c->box_L;
+    p.x_prev = c->x_prev;
+    p.r_prev = c->r_prev;
+    p.u_prev = c->u_prev;
+    p.slab32 = c->slab32;
+    p.slab64 = c->slab64;
+    p.anchors = c->anchors;
+    p.ncols = c->ncols;
+    p.ring = c->ring;
+    p.K = c->K;
+    p.nblk = c->nblk;
+    p.n_species = c->n_species;
+    for (int s = 0; s <= c->n_species; ++s) p.in_off[s] = c->in_off[s];
+    for (int s = 0; s < c->n_species; ++s) p.col_off[s] = c->col_off[s];
+    p.check = c->opt.check_inputs;
+    p.err_word = c->d_err;
+    int64_t s = step0;
+    const int64_t end = step0 + n;
+    while (s < end) {
+        // split at the next closing call so windows close right after their last sample
+        int64_t stop = end;
+        if (!c->opt.defer) {
+            auto itv = c->event_at.lower_bound(s);
+            if (itv != c->event_at.end() && itv->first < end) stop = itv->first + 1;
+        }
+        p.x = x + (s - step0) * 3 * c->n_in;
+        p.u = u + (s - step0) * 3 * c->n_in;
+        p.step0 = s;
+        p.n_steps = (int32_t)(stop - s);
+        cudaEvent_t e0 = nullptr;
+        if (c->time_ingest) {
+            e0 = next_event(c->ing_ev, c->ing_used, true);
+            CU(cudaEventRecord(e0, c->stream));
+        }
+        cudaError_t e = launch_ingest(p, c->stream);
+        if (e != cudaSuccess) return fail(c, RAD_ECUDA, "ingest launch failed: %s", cudaGetErrorString(e));
+        if (c->time_ingest) CU(cudaEventRecord(next_event(c->ing_ev, c->ing_used, false), c->stream));
+        ++c->ing_launches;
+        if (!c->opt.defer) {
+            auto itv = c->event_at.find(stop - 1);
+            if (itv != c->event_at.end()) {
+                int rc = launch_event(c, c->events[itv->second]);
+                if (rc) return rc;
+            }
+        }
+        s = stop;
+    }
+    return RAD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int rad_init(rad_ctx** out, const double* dirs, int32_t D, const double* freqs,
+             const int32_t* grid_len, int32_t n_grids, double dt, const rad_species* sp,
+             int32_t n_species, const rad_window* win, int32_t n_win, int32_t mode,
+             int32_t precision, double box_L, void* cuda_stream)
+{
+    if (!out) return RAD_EINVAL;
+    *out = nullptr;
+    if (!dirs || D < 1 || !freqs || !grid_len || n_grids < 1 || !(dt > 0.0) || !std::isfinite(dt) ||
+        !sp || n_species < 1 || n_species > kMaxSpecies || !win || n_win < 1 ||
+        (mode != RAD_INCOHERENT && mode != RAD_COHERENT) ||
+        (precision != RAD_FP64 && precision != RAD_FP32_SPLIT) || !(box_L >= 0.0) ||
+        !std::isfinite(box_L))
+        return RAD_EINVAL;
+    rad_ctx* c = new (std::nothrow) rad_ctx();
+    if (!c) return RAD_ENOMEM;
+    auto bail = [&](int rc) {
+        rad_destroy(c);
+        return rc;
+    };
+    c->D = D;
+    c->n_grids = n_grids;
+    c->dt = dt;
+    c->box_L = box_L;
+    c->mode = mode;
+    c->precision = precision;
+    c->n_species = n_species;
+    c->stream = (cudaStream_t)cuda_stream;
+    int64_t nf = 0;
+    for (int g = 0; g < n_grids; ++g) {
+        if (grid_len[g] < 1) return bail(RAD_EINVAL);
+        c->grid_off.push_back((int)nf);
+        c->grid_len.push_back(grid_len[g]);
+        nf += grid_len[g];
+    }
+    for (int64_t i = 0; i < nf; ++i)
+        if (!std::isfinite(freqs[i])) return bail(RAD_EINVAL);
+    c->in_off.push_back(0);
+    int64_t col = 0;
+    for (int s = 0; s < n_species; ++s) {
+        if (sp[s].count < 0 || !std::isfinite(sp[s].charge)) return bail(RAD_EINVAL);
+        c->species.push_back(sp[s]);
+        c->col_off.push_back((int32_t)col);
+        col += (sp[s].count + kTileP - 1) / kTileP * kTileP;
+        c->in_off.push_back(c->in_off.back() + sp[s].count);
+    }
+    c->n_in = c->in_off.back();
+    c->ncols = std::max<int64_t>(col, kTileP);
+    if (c->ncols > (int64_t)1 << 30) return bail(RAD_EINVAL);
+    int64_t min_s0 = INT64_MAX;
+    for (int w = 0; w < n_win; ++w) {
+        const rad_window& W = win[w];
+        if (W.s0 < 0 || W.s1 < W.s0 || W.freq_grid < 0 || W.freq_grid >= n_grids ||
+            (n_species < 32 && (W.species_mask >> n_species) != 0))
+            return bail(RAD_EINVAL);
+        c->wins.push_back(W);
+        c->out_off.push_back(c->out_len);
+        c->out_len += (int64_t)D * grid_len[W.freq_grid];
+        c->max_s1 = std::max<int64_t>(c->max_s1, W.s1);
+        min_s0 = std::min<int64_t>(min_s0, W.s0);
+    }
+    // ring length: longest window (eager) or the whole span (defer is decided
+    // later, so size for the span; the ring is what the windows need at once)
+    int64_t span = std::max<int64_t>(1, c->max_s1 - min_s0);
+    c->ring = (span + 31) / 32 * 32 + 64;
+
+    int rc;
+    {
+        int dev;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return bail(fail(c, RAD_ECUDA, "no CUDA device: %s", cudaGetErrorString(e)));
+        c->device = dev;
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return bail(RAD_ECUDA);
+        c->sms = prop.multiProcessorCount;
+    }
+    (void)rc;
+#define CUB(call)                                                      \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess)                                         \
+            return bail(e_ == cudaErrorMemoryAllocation ? RAD_ENOMEM : RAD_ECUDA); \
+    } while (0)
+    // directions and bases
+    std::vector<float> d32((size_t)D * 9);
+    std::vector<double> d64n((size_t)D * 3), d64((size_t)D * 9);
+    for (int d = 0; d < D; ++d) {
+        double n[3] = {dirs[3 * d], dirs[3 * d + 1], dirs[3 * d + 2]};
+        double l = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        if (!(l > 0.0) || !std::isfinite(l)) return bail(RAD_EINVAL);
+        for (int i = 0; i < 3; ++i) n[i] /= l;
+        double e1[3], e2[3];
+        basis(n, e1, e2);
+        for (int i = 0; i < 3; ++i) {
+            d32[9 * d + i] = (float)n[i];
+            d32[9 * d + 3 + i] = (float)e1[i];
+            d32[9 * d + 6 + i] = (float)e2[i];
+            d64n[3 * d + i] = n[i];
+            d64[9 * d + i] = n[i];
+            d64[9 * d + 3 + i] = e1[i];
+            d64[9 * d + 6 + i] = e2[i];
+        }
+    }
+    std::vector<float> om32(nf), nuh(nf), nul(nf);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int64_t i = 0; i < nf; ++i) {
+        om32[i] = (float)freqs[i];
+        const double nu = freqs[i] / two_pi;
+        nuh[i] = (float)nu;
+        nul[i] = (float)(nu - (double)nuh[i]);
+    }
+    std::vector<WinDev> wd(n_win);
+    for (int w = 0; w < n_win; ++w) {
+        wd[w].s0 = win[w].s0;
+        wd[w].s1 = win[w].s1;
+        wd[w].grid_off = c->grid_off[win[w].freq_grid];
+        wd[w].grid_len = c->grid_len[win[w].freq_grid];
+        wd[w].out_off = c->out_off[w];
+    }
+    std::vector<SpeciesDev> sd(n_species);
+    for (int s = 0; s < n_species; ++s) {
+        sd[s].qdt = sp[s].charge * dt;
+        sd[s].col0 = c->col_off[s];
+        sd[s].count = (int32_t)sp[s].count;
+    }
+    CUB(cudaMalloc(&c->d_dirs32, d32.size() * sizeof(float)));
+    CUB(cudaMalloc(&c->d_dirs64n, d64n.size() * sizeof(double)));
+    CUB(cudaMalloc(&c->d_dirs64, d64.size() * sizeof(double)));
+    CUB(cudaMalloc(&c->d_om32, nf * sizeof(float)));
+    CUB(cudaMalloc(&c->d_nuhi, nf * sizeof(float)));
+    CUB(cudaMalloc(&c->d_nulo, nf * sizeof(float)));
+    CUB(cudaMalloc(&c->d_om64, nf * sizeof(double)));
+    CUB(cudaMalloc(&c->d_wins, n_win * sizeof(WinDev)));
+    CUB(cudaMalloc(&c->d_species, n_species * sizeof(SpeciesDev)));
+    CUB(cudaMemcpy(c->d_dirs32, d32.data(), d32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CUB(cudaMemcpy(c->d_dirs64n, d64n.data(), d64n.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CUB(cudaMemcpy(c->d_dirs64, d64.data(), d64.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CUB(cudaMemcpy(c->d_om32, om32.data(), nf * sizeof(float), cudaMemcpyHostToDevice));
+    CUB(cudaMemcpy(c->d_nuhi, nuh.data(), nf * sizeof(float), cudaMemcpyHostToDevice));
+    CUB(cudaMemcpy(c->d_nulo, nul.data(), nf * sizeof(float), cudaMemcpyHostToDevice));
+    CUB(cudaMemcpy(c->d_om64, freqs, nf * sizeof(double), cudaMemcpyHostToDevice));
+    CUB(cudaMemcpy(c->d_wins, wd.data(), n_win * sizeof(WinDev), cudaMemcpyHostToDevice));
+    CUB(cudaMemcpy(c->d_species, sd.data(), n_species * sizeof(SpeciesDev), cudaMemcpyHostToDevice));
+
+    // ring and state
+    const int64_t nc = c->ncols;
+    if (precision == RAD_FP64) {
+        CUB(cudaMalloc(&c->slab64, (size_t)c->ring * kComps * nc * sizeof(double)));
+        CUB(cudaMemset(c->slab64, 0, (size_t)c->ring * kComps * nc * sizeof(double)));
+    } else {
+        CUB(cudaMalloc(&c->slab32, (size_t)c->ring * kComps * nc * sizeof(float)));
+        CUB(cudaMemset(c->slab32, 0, (size_t)c->ring * kComps * nc * sizeof(float)));
+    }
+    CUB(cudaMalloc(&c->x_prev, 3 * nc * sizeof(double)));
+    CUB(cudaMalloc(&c->r_prev, 3 * nc * sizeof(double)));
+    CUB(cudaMalloc(&c->u_prev, 3 * nc * sizeof(double)));
+    const size_t acc_n = (size_t)c->out_len * (mode == RAD_COHERENT ? 4 : 1);
+    CUB(cudaMalloc(&c->acc, std::max<size_t>(1, acc_n) * sizeof(double)));
+    CUB(cudaMemset(c->acc, 0, std::max<size_t>(1, acc_n) * sizeof(double)));
+    CUB(cudaMalloc(&c->d_out, std::max<int64_t>(1, c->out_len) * sizeof(double)));
+    CUB(cudaMalloc(&c->d_err, sizeof(int)));
+    CUB(cudaMemset(c->d_err, 0, sizeof(int)));
+    CUB(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+        CUB(cudaEventCreateWithFlags(&c->copy_done[b], cudaEventDisableTiming));
+        CUB(cudaEventCreateWithFlags(&c->used_done[b], cudaEventDisableTiming));
+    }
+    CUB(cudaDeviceSynchronize());
+#undef CUB
+    *out = c;
+    return RAD_OK;
+}
+
+int rad_set_options(rad_ctx* c, const rad_options* o)
+{
+    if (!c || !o) return RAD_EINVAL;
+    if (c->frozen) return fail(c, RAD_ESTATE, "options must be set before the first step");
+    if (o->variant < 0 || o->variant > 2) return fail(c, RAD_EINVAL, "variant out of range");
+    if (o->anchor_K != 0 && o->anchor_K != 8 && o->anchor_K != 16 && o->anchor_K != 32)
+        return fail(c, RAD_EINVAL, "anchor_K must be 0, 8, 16 or 32");
+    if (o->freq_per_lane != 0 && o->freq_per_lane != 8 && o->freq_per_lane != 16)
+        return fail(c, RAD_EINVAL, "freq_per_lane must be 0, 8 or 16");
+    if (o->mix_sfu_of_16 < 0 || o->mix_sfu_of_16 > 16)
+        return fail(c, RAD_EINVAL, "mix_sfu_of_16 must be in [0, 16]");
+    c->opt = *o;
+    c->time_ingest = o->reserved[0] != 0;
+    return RAD_OK;
+}
+
+int rad_get_options(const rad_ctx* c, rad_options* o)
+{
+    if (!c || !o) return RAD_EINVAL;
+    *o = c->opt;
+    if (c->frozen && c->precision == RAD_FP32_SPLIT) {
+        o->anchor_K = c->K;
+        o->freq_per_lane = c->ft;
+        if (o->variant == RAD_VARIANT_AUTO) o->variant = RAD_VARIANT_SFU;
+    }
+    return RAD_OK;
+}
+
+int rad_accumulate_steps(rad_ctx* c, int64_t step0, int64_t n, const double* x, const double* u)
+{
+    if (!c) return RAD_EINVAL;
+    if (n < 0 || (n > 0 && (!x || !u))) return fail(c, RAD_EINVAL, "bad step count or null input");
+    if (step0 != c->next_step)
+        return fail(c, RAD_ESTEP, "step %lld given, %lld expected", (long long)step0,
+                    (long long)c->next_step);
+    if (n == 0) return RAD_OK;
+    int rc = freeze(c);
+    if (rc) return rc;
+    CU(cudaSetDevice(c->device));
+    const bool dx = is_device_ptr(x), du = is_device_ptr(u);
+    if (dx && du) {
+        rc = ingest_device(c, step0, n, x, u);
+        if (rc) return rc;
+    } else {
+        // host inputs: double-buffered staging on a copy stream
+        const int64_t per = 3 * c->n_in;
+        int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n, 64));
+        if (c->stage_steps < chunk) {
+            for (int b = 0; b < 2; ++b) {
+                if (c->stage[b]) {
+                    CU(cudaStreamSynchronize(c->stream));
+                    CU(cudaFree(c->stage[b]));
+                    c->stage[b] = nullptr;
+                }
+                CU(cudaMalloc(&c->stage[b], (size_t)std::max<int64_t>(1, 2 * chunk * per) * sizeof(double)));
+            }
+            c->stage_steps = chunk;
+        }
+        for (int64_t s = 0; s < n; s += chunk) {
+            const int64_t m = std::min(chunk, n - s);
+            const int b = c->stage_next;
+            c->stage_next ^= 1;
+            double* sx = c->stage[b];
+            double* su = c->stage[b] + c->stage_steps * per;
+            CU(cudaStreamWaitEvent(c->copy_stream, c->used_done[b], 0));
+            const size_t bytes = (size_t)m * per * sizeof(double);
+            if (dx) CU(cudaMemcpyAsync(sx, x + s * per, bytes, cudaMemcpyDeviceToDevice, c->copy_stream));
+            else CU(cudaMemcpyAsync(sx, x + s * per, bytes, cudaMemcpyHostToDevice, c->copy_stream));
+            if (du) CU(cudaMemcpyAsync(su, u + s * per, bytes, cudaMemcpyDeviceToDevice, c->copy_stream));
+            else CU(cudaMemcpyAsync(su, u + s * per, bytes, cudaMemcpyHostToDevice, c->copy_stream));
+            CU(cudaEventRecord(c->copy_done[b], c->copy_stream));
+            CU(cudaStreamWaitEvent(c->stream, c->copy_done[b], 0));
+            rc = ingest_device(c, step0 + s, m, sx, su);
+            if (rc) return rc;
+            CU(cudaEventRecord(c->used_done[b], c->stream));
+        }
+        // the caller may reuse its host buffers once this returns
+        CU(cudaStreamSynchronize(c->copy_stream));
+    }
+    c->next_step = step0 + n;
+    return RAD_OK;
+}
+
+int rad_accumulate(rad_ctx* c, int64_t step, const double* x, const double* u)
+{
+    return rad_accumulate_steps(c, step, 1, x, u);
+}
+
+int rad_finalize(rad_ctx* c, double* spectrum)
+{
+    if (!c) return RAD_EINVAL;
+    if (!spectrum && c->out_len > 0) return fail(c, RAD_EINVAL, "null spectrum buffer");
+    if (c->next_step < c->max_s1 + 1)
+        return fail(c, RAD_EINCOMPLETE, "window needs step %lld, last step given is %lld",
+                    (long long)c->max_s1, (long long)c->next_step - 1);
+    int rc = freeze(c);
+    if (rc) return rc;
+    CU(cudaSetDevice(c->device));
+    if (c->opt.defer && !c->deferred_done) {
+        for (auto& ev : c->events) {
+            rc = launch_event(c, ev);
+            if (rc) return rc;
+        }
+        c->deferred_done = true;
+    }
+    if (c->out_len > 0) {
+        finalize_kernel<<<(unsigned)std::min<int64_t>((c->out_len + 255) / 256, 4096), 256, 0, c->stream>>>(
+            c->acc, c->d_out, c->out_len, c->mode == RAD_COHERENT);
+        CU(cudaGetLastError());
+        const bool dev = is_device_ptr(spectrum);
+        CU(cudaMemcpyAsync(spectrum, c->d_out, c->out_len * sizeof(double),
+                           dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    }
+    int errw = 0;
+    CU(cudaMemcpyAsync(&errw, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (errw & kErrTimeout) return fail(c, RAD_ETIMEOUT, "a device-side wait expired");
+    if (errw & kErrNaN) return fail(c, RAD_ENAN, "non-finite x or u in the input");
+    return RAD_OK;
+}
+
+int rad_reset(rad_ctx* c)
+{
+    if (!c) return RAD_EINVAL;
+    CU(cudaSetDevice(c->device));
+    const size_t acc_n = (size_t)c->out_len * (c->mode == RAD_COHERENT ? 4 : 1);
+    CU(cudaMemsetAsync(c->acc, 0, std::max<size_t>(1, acc_n) * sizeof(double), c->stream));
+    CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    c->next_step = 0;
+    c->deferred_done = false;
+    c->acc_used = c->ing_used = 0;
+    c->acc_launches = c->ing_launches = 0;
+    return RAD_OK;
+}
+
+int64_t rad_spectrum_size(const rad_ctx* c) { return c ? c->out_len : -1; }
+
+int64_t rad_updates(const rad_ctx* c)
+{
+    if (!c) return -1;
+    int64_t tot = 0;
+    for (const auto& W : c->wins) {
+        int64_t np = 0;
+        for (int s = 0; s < c->n_species; ++s)
+            if ((W.species_mask >> s) & 1u) np += c->species[s].count;
+        tot += np * (W.s1 - W.s0) * c->D * c->grid_len[W.freq_grid];
+    }
+    return tot;
+}
+
+int rad_timing(rad_ctx* c, double* accum_ms, double* ingest_ms, int64_t* accum_launches,
+               int64_t* ingest_launches)
+{
+    if (!c) return RAD_EINVAL;
+    CU(cudaSetDevice(c->device));
+    CU(cudaStreamSynchronize(c->stream));
+    double a = 0, g = 0;
+    for (size_t i = 0; i < c->acc_used; ++i) {
+        float ms = 0;
+        CU(cudaEventElapsedTime(&ms, c->acc_ev[i].first, c->acc_ev[i].second));
+        a += ms;
+    }
+    for (size_t i = 0; i < c->ing_used; ++i) {
+        float ms = 0;
+        CU(cudaEventElapsedTime(&ms, c->ing_ev[i].first, c->ing_ev[i].second));
+        g += ms;
+    }
+    if (accum_ms) *accum_ms = a;
+    if (ingest_ms) *ingest_ms = g;
+    if (accum_launches) *accum_launches = c->acc_launches;
+    if (ingest_launches) *ingest_launches = c->ing_launches;
+    return RAD_OK;
+}
+
+const char* rad_last_error(const rad_ctx* c)
+{
+    if (!c) return kNoCtx;
+    return c->err.c_str();
+}
+
+void rad_destroy(rad_ctx* c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto& ev : c->events) cudaFree(ev.d_items);
+    void* bufs[] = {c->slab32, c->slab64, c->anchors, c->x_prev, c->r_prev, c->u_prev,
+                    c->d_dirs32, c->d_dirs64n, c->d_dirs64, c->d_om32, c->d_nuhi, c->d_nulo,
+                    c->d_om64, c->d_wins, c->d_species, c->acc, c->d_out, c->d_err,
+                    c->stage[0], c->stage[1]};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    for (auto& pr : c->acc_ev) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    for (auto& pr : c->ing_ev) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    for (int b = 0; b < 2; ++b) {
+        if (c->copy_done[b]) cudaEventDestroy(c->copy_done[b]);
+        if (c->used_done[b]) cudaEventDestroy(c->used_done[b]);
+    }
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    delete c;
+}
+
+}  // extern "C"

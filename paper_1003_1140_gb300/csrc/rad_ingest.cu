@@ -1,0 +1,142 @@
+// rad_ingest.cu -- per-step ingest: leapfrog states -> trajectory ring.
+//
+// Sec. 2.2 integrates E_ret exp(i w phi') over the particle history.  This
+// kernel turns the states the PIC hands over (call s: x_s, u_{s-1/2}) into
+// the samples the accumulation needs, one call late: sample m = s - 1 uses
+//   r_m       = unwrapped x_m (minimum image in a periodic box),
+//   beta_m    = ubar / sqrt(1 + ubar^2),  ubar = (u_{m-1/2} + u_{m+1/2}) / 2,
+//   betadot_m = (beta_{m+1/2} - beta_{m-1/2}) / dt   (FP64, before rounding),
+//   g_m       = 1/gamma_m^2 = 1 / (1 + ubar^2).
+// One thread per particle walks the launch's steps in order, keeping the
+// previous raw position, the unwrapped position and u_{s-3/2} in registers
+// and in the per-particle state arrays between launches.
+#include "rad_internal.cuh"
+
+namespace rad {
+
+__device__ __forceinline__ double min_image(double d, double L)
+{
+    return L > 0.0 ? d - L * rint(d / L) : d;
+}
+
+__global__ void __launch_bounds__(256) ingest_kernel(const IngestParams p)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= p.n_in) return;
+    int sp = 0;
+    while (sp + 1 < p.n_species && i >= p.in_off[sp + 1]) ++sp;
+    const int64_t col = p.col_off[sp] + (i - p.in_off[sp]);
+    const int64_t nc = p.ncols;
+
+    double xp[3], rp[3], up[3], ra[3];
+    bool have_state = p.step0 > 0;
+    if (have_state) {
+        for (int c = 0; c < 3; ++c) {
+            xp[c] = p.x_prev[c * nc + col];
+            rp[c] = p.r_prev[c * nc + col];
+            up[c] = p.u_prev[c * nc + col];
+        }
+    }
+    bool have_anchor = false;
+    bool bad = false;
+
+    for (int t = 0; t < p.n_steps; ++t) {
+        const int64_t s = p.step0 + t;
+        const double* xs = p.x + (int64_t)t * 3 * p.n_in;
+        const double* us = p.u + (int64_t)t * 3 * p.n_in;
+        double xn[3], un[3], rn[3];
+        for (int c = 0; c < 3; ++c) {
+            xn[c] = xs[c * p.n_in + i];
+            un[c] = us[c * p.n_in + i];
+        }
+        if (p.check) {
+            for (int c = 0; c < 3; ++c) bad |= !isfinite(xn[c]) || !isfinite(un[c]);
+        }
+        if (s == 0) {
+            for (int c = 0; c < 3; ++c) {
+                xp[c] = xn[c];
+                rp[c] = xn[c];
+                up[c] = un[c];
+            }
+            continue;
+        }
+        // unwrapped position of this call
+        for (int c = 0; c < 3; ++c) rn[c] = rp[c] + min_image(xn[c] - xp[c], p.box_L);
+
+        // sample m = s - 1: r_m = rp, u_{m-1/2} = up, u_{m+1/2} = un
+        const int64_t m = s - 1;
+        double ub[3];
+        for (int c = 0; c < 3; ++c) ub[c] = 0.5 * (up[c] + un[c]);
+        const double gm = sqrt(1.0 + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
+        const double gp = sqrt(1.0 + (un[0] * un[0] + un[1] * un[1] + un[2] * un[2]));
+        const double gb2 = 1.0 + (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
+        const double gb = sqrt(gb2);
+        double beta[3], bdot[3];
+        for (int c = 0; c < 3; ++c) {
+            beta[c] = ub[c] / gb;
+            bdot[c] = (un[c] / gp - up[c] / gm) / p.dt;
+        }
+        const double g = 1.0 / gb2;
+        const int64_t slot = m % p.ring;
+
+        if (p.slab32) {
+            if ((m % p.K) == 0) {
+                const int64_t blk = (m / p.K) % p.nblk;
+                for (int c = 0; c < 3; ++c) {
+                    ra[c] = rp[c];
+                    p.anchors[(blk * 3 + c) * nc + col] = rp[c];
+                }
+                have_anchor = true;
+            } else if (!have_anchor) {
+                const int64_t blk = (m / p.K) % p.nblk;
+                for (int c = 0; c < 3; ++c) ra[c] = p.anchors[(blk * 3 + c) * nc + col];
+                have_anchor = true;
+            }
+            float* o = p.slab32 + slot * kComps * nc + col;
+            o[0 * nc] = (float)(rp[0] - ra[0]);
+            o[1 * nc] = (float)(rp[1] - ra[1]);
+            o[2 * nc] = (float)(rp[2] - ra[2]);
+            o[3 * nc] = (float)beta[0];
+            o[4 * nc] = (float)beta[1];
+            o[5 * nc] = (float)beta[2];
+            o[6 * nc] = (float)bdot[0];
+            o[7 * nc] = (float)bdot[1];
+            o[8 * nc] = (float)bdot[2];
+            o[9 * nc] = (float)g;
+        } else {
+            double* o = p.slab64 + slot * kComps * nc + col;
+            o[0 * nc] = rp[0];
+            o[1 * nc] = rp[1];
+            o[2 * nc] = rp[2];
+            o[3 * nc] = beta[0];
+            o[4 * nc] = beta[1];
+            o[5 * nc] = beta[2];
+            o[6 * nc] = bdot[0];
+            o[7 * nc] = bdot[1];
+            o[8 * nc] = bdot[2];
+            o[9 * nc] = g;
+        }
+        for (int c = 0; c < 3; ++c) {
+            xp[c] = xn[c];
+            rp[c] = rn[c];
+            up[c] = un[c];
+        }
+    }
+    for (int c = 0; c < 3; ++c) {
+        p.x_prev[c * nc + col] = xp[c];
+        p.r_prev[c * nc + col] = rp[c];
+        p.u_prev[c * nc + col] = up[c];
+    }
+    if (bad) atomicOr(p.err_word, kErrNaN);
+}
+
+cudaError_t launch_ingest(const IngestParams& p, cudaStream_t st)
+{
+    if (p.n_in == 0 || p.n_steps == 0) return cudaSuccess;
+    const int threads = 256;
+    const int64_t blocks = (p.n_in + threads - 1) / threads;
+    ingest_kernel<<<(unsigned)blocks, threads, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace rad

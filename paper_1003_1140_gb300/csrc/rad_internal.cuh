@@ -1,0 +1,215 @@
+// rad_internal.cuh -- structures and sm_103a device helpers shared by the
+// kernels of the radiation-spectrum library (not part of the public ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rad {
+
+// ---------------------------------------------------------------------------
+// trajectory ring layout
+// ---------------------------------------------------------------------------
+// FP32 split path: slab[slot][c][col] float, c = 0..9 =
+//   dr (3)   : r_m - r_a, the offset from the block's FP64 anchor position
+//   beta (3) : beta_m
+//   bdot (3) : betadot_m (differenced in FP64 before the rounding)
+//   g (1)    : 1/gamma_m^2 = 1/(1 + ubar^2)
+// anchors[blk][c][col] double: r_a at samples a = K * blk (ring of blocks).
+// FP64 path: slab64[slot][c][col] double with c = r (3, absolute unwrapped),
+// beta (3), bdot (3), g (1).
+constexpr int kComps = 10;
+constexpr int kTileP = 8;      // particles per tile: one warp each
+constexpr int kChunk32 = 32;   // samples per TMA chunk, FP32 ring
+constexpr int kChunk64 = 16;   // samples per TMA chunk, FP64 ring
+constexpr int kComputeWarps = 8;
+constexpr int kBlockThreads = (kComputeWarps + 1) * 32;  // + one TMA producer warp
+constexpr int kMaxSpecies = 32;
+
+// error word bits
+constexpr int kErrTimeout = 1;
+constexpr int kErrNaN = 2;
+
+// One unit of accumulation work: a window, a direction, a tile of the
+// frequency grid and a run of particle tiles of one species.
+struct WorkItem {
+    int32_t win;      // window index
+    int32_t dir;      // direction index
+    int32_t ftile;    // frequency tile index within the window's grid
+    int32_t sp;       // species index
+    int32_t tile0;    // first particle tile (column / 8)
+    int32_t ntiles;   // number of particle tiles
+};
+
+// Per-window constants the accumulation kernels read.
+struct WinDev {
+    int64_t s0, s1;      // sample range
+    int32_t grid_off;    // offset of the frequency grid in the frequency arrays
+    int32_t grid_len;    // frequencies in the grid
+    int64_t out_off;     // offset of the window's [D][len] block in the accumulators
+};
+
+struct SpeciesDev {
+    double qdt;          // q * dt
+    int32_t col0;        // first column of the species in the ring
+    int32_t count;       // particles
+};
+
+// ---------------------------------------------------------------------------
+// mbarrier / TMA helpers (inline PTX, sm_90+ forms valid on sm_103a)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
+        "r"(bytes)
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: spins with a growing back-off for at most ~2^22 polls
+// (about a second).  On expiry it raises the block's abort flag and the
+// device error word, and returns false; callers then carry on without
+// waiting (results are flagged invalid) so that no thread is left behind at
+// a barrier.
+constexpr uint32_t kMaxPolls = 1u << 22;
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  volatile int* s_abort, int* err_word)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    for (uint32_t it = 0; it < kMaxPolls; ++it) {
+        if (*s_abort) return false;
+        if (mbar_try_wait(bar, parity)) return true;
+        __nanosleep(it < 64 ? 32 : 256);
+    }
+    *s_abort = 1;
+    atomicOr(err_word, kErrTimeout);
+    return false;
+}
+
+// 3-D tiled TMA load of one box into shared memory, completion on `bar`.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y,
+                                            int z, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_addr(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
+__device__ __forceinline__ void named_barrier_sync(int id, int count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+
+// ---------------------------------------------------------------------------
+// kernel parameter blocks and launchers
+// ---------------------------------------------------------------------------
+struct IngestParams {
+    const double* x;        // [n_steps][3][n_in]
+    const double* u;        // [n_steps][3][n_in]
+    int64_t n_in;           // particles on the input axis
+    int32_t n_steps;
+    int64_t step0;          // absolute step of the first state in x/u
+    double dt;
+    double box_L;           // 0: no unwrapping
+    double* x_prev;         // [3][ncols] raw x of the previous call
+    double* r_prev;         // [3][ncols] unwrapped x of the previous call
+    double* u_prev;         // [3][ncols] u of the previous call
+    float* slab32;          // FP32 ring or nullptr
+    double* slab64;         // FP64 ring or nullptr
+    double* anchors;        // FP32 path: [nblk][3][ncols] r at anchor samples
+    int64_t ncols;
+    int64_t ring;           // samples in the ring
+    int32_t K;              // anchor interval (FP32 path)
+    int64_t nblk;           // anchor blocks in the ring
+    int32_t n_species;
+    int64_t in_off[kMaxSpecies + 1];
+    int32_t col_off[kMaxSpecies];
+    int32_t check;          // flag non-finite inputs
+    int* err_word;
+};
+
+struct Accum32Params {
+    const WorkItem* items;
+    int32_t n_items;
+    const WinDev* wins;
+    const SpeciesDev* species;
+    const float* dirs32;      // [D][9]: n, e1, e2
+    const double* dirs64;     // [D][3]: n
+    const float* omega;       // [n_freq] rad per unit time
+    const float* nu_hi;       // [n_freq] (omega / 2 pi) hi part
+    const float* nu_lo;       // [n_freq] lo part
+    const double* anchors;    // [nblk][3][ncols]
+    int64_t ncols;
+    int64_t ring;
+    int64_t nblk;
+    double dt;
+    double* acc;              // incoherent [n_out]; coherent [n_out][4]
+    int* err_word;
+};
+
+struct Accum64Params {
+    const WorkItem* items;
+    int32_t n_items;
+    const WinDev* wins;
+    const SpeciesDev* species;
+    const double* dirs64;     // [D][9]: n, e1, e2
+    const double* omega;      // [n_freq]
+    int64_t ring;
+    double dt;
+    double* acc;
+    int* err_word;
+};
+
+cudaError_t launch_ingest(const IngestParams& p, cudaStream_t st);
+cudaError_t launch_accum32(const CUtensorMap& tmap, const Accum32Params& p, int ft, int K,
+                           bool coh, int grid, cudaStream_t st);
+int accum32_blocks_per_sm(int ft, int K, bool coh);
+cudaError_t launch_accum64(const CUtensorMap& tmap, const Accum64Params& p, bool coh, int grid,
+                           cudaStream_t st);
+int accum64_blocks_per_sm(bool coh);
+int accum64_ft();
+
+}  // namespace rad

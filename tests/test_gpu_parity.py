@@ -1,0 +1,210 @@
+"""CUDA path (through the C ABI) against the FP64 CPU oracle on identical inputs.
+
+Tolerances: FP64 GPU path within 1e-10 relative L2 of the oracle; FP32
+split-phase path within 1e-4 relative L2 per (window, direction) spectrum.
+Sizes span several particle tiles (8), frequency tiles (256 / 128) and
+sample chunks (32 / 16), each with a ragged tail.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import trajgen
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _rad():
+    import paper_1003_1140_gb300 as R
+    return R
+
+
+def relL2(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def two_species():
+    """29 electrons (gamma 3) + 11 ions (m = 16, q = +1), 301 calls."""
+    w = trajgen.Workload("two-species", [(29, -1.0, 1.0, 3.0), (11, 1.0, 16.0, 3.0)], 301, 0.05,
+                         np.array([[0.0, 1.0, 0.0], [1.0, 0, 0], [-1.0, 0, 0],
+                                   [0.6, 0.0, 0.8], [1 / math.sqrt(3)] * 3]),
+                         [trajgen.log_grid(0.1, 300.0, 300), np.linspace(0.5, 20.0, 37)],
+                         [(0, 300, 3, 0), (17, 250, 1, 1), (100, 100, 3, 0), (33, 64, 2, 0)],
+                         b_rms=0.3)
+    X, U = w.trajectory_numpy()
+    species = [(s[0], s[1]) for s in w.species]
+    ref = {}
+    for coh in (False, True):
+        ref[coh] = oracle.spectra(X, U, w.dt, w.dirs, w.grids, w.windows, species,
+                                  coherent=coh, box_L=w.L)
+    return w, X, U, ref
+
+
+def _run(w, X, U, precision, coherent=False, options=None, device_inputs=True, steps=True):
+    R = _rad()
+    sp = [(s[0], s[1], s[2]) for s in w.species]
+    r = R.Radiation(w.dirs, w.grids, w.dt, sp, w.windows,
+                    mode=R.RAD_COHERENT if coherent else R.RAD_INCOHERENT,
+                    precision=precision, box_L=w.L, options=options)
+    if device_inputs:
+        Xi = torch.as_tensor(X, device="cuda")
+        Ui = torch.as_tensor(U, device="cuda")
+    else:
+        Xi, Ui = np.ascontiguousarray(X), np.ascontiguousarray(U)
+    if steps:
+        r.accumulate_steps(0, Xi, Ui)
+    else:
+        for s in range(X.shape[0]):
+            r.accumulate(s, Xi[s], Ui[s])
+    out = r.finalize()
+    r.close()
+    return out
+
+
+def _check(got, ref, tol, per_direction):
+    for g, e in zip(got, ref):
+        assert g.shape == e.shape
+        if not np.any(e):
+            assert np.all(g == 0.0)
+            continue
+        if per_direction:
+            for d in range(e.shape[0]):
+                assert relL2(g[d], e[d]) <= tol, (d, relL2(g[d], e[d]))
+        else:
+            assert relL2(g, e) <= tol, relL2(g, e)
+
+
+@pytest.mark.parametrize("coherent", [False, True])
+def test_fp64_matches_oracle(two_species, coherent):
+    R = _rad()
+    w, X, U, ref = two_species
+    got = _run(w, X, U, R.RAD_FP64, coherent)
+    _check(got, ref[coherent], 1e-10, per_direction=True)
+
+
+@pytest.mark.parametrize("coherent", [False, True])
+@pytest.mark.parametrize("K", [8, 16, 32])
+def test_fp32_split_matches_oracle(two_species, coherent, K):
+    R = _rad()
+    w, X, U, ref = two_species
+    got = _run(w, X, U, R.RAD_FP32_SPLIT, coherent, options={"anchor_K": K})
+    _check(got, ref[coherent], 1e-4, per_direction=True)
+
+
+def test_fp32_split_sixteen_freq_per_lane(two_species):
+    R = _rad()
+    w, X, U, ref = two_species
+    got = _run(w, X, U, R.RAD_FP32_SPLIT, options={"freq_per_lane": 16})
+    _check(got, ref[False], 1e-4, per_direction=True)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_host_inputs_and_single_steps_agree(two_species, precision):
+    w, X, U, _ = two_species
+    a = _run(w, X, U, precision, device_inputs=True, steps=True)
+    b = _run(w, X, U, precision, device_inputs=False, steps=False)
+    for g, e in zip(a, b):
+        np.testing.assert_allclose(g, e, rtol=1e-12, atol=1e-300)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_defer_matches_eager(two_species, precision):
+    w, X, U, _ = two_species
+    a = _run(w, X, U, precision)
+    b = _run(w, X, U, precision, options={"defer": 1})
+    for g, e in zip(a, b):
+        np.testing.assert_allclose(g, e, rtol=1e-12, atol=1e-300)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_uniform_motion_is_exactly_zero_on_gpu(precision):
+    R = _rad()
+    rng = np.random.default_rng(3)
+    N, nc, dt = 13, 70, 0.05
+    u0 = rng.normal(size=(3, N))
+    g = np.sqrt(1 + (u0 ** 2).sum(0))
+    U = np.ascontiguousarray(np.broadcast_to(u0, (nc, 3, N)))
+    X = np.stack([rng.uniform(0, 40, (3, N)) + s * dt * u0 / g for s in range(nc)])
+    X = np.ascontiguousarray(X - 40.0 * np.floor(X / 40.0))
+    for coh in (R.RAD_INCOHERENT, R.RAD_COHERENT):
+        with R.Radiation(trajgen.axis_and_oblique_dirs(), [trajgen.log_grid(0.1, 300, 50)], dt,
+                         [(N, -1.0)], [(0, nc - 1, 1, 0)], mode=coh, precision=precision,
+                         box_L=40.0) as r:
+            r.accumulate_steps(0, X, U)
+            S = r.finalize()[0]
+        assert np.all(S == 0.0)
+
+
+def test_finalize_twice_and_reset(two_species):
+    R = _rad()
+    w, X, U, ref = two_species
+    sp = [(s[0], s[1], s[2]) for s in w.species]
+    with R.Radiation(w.dirs, w.grids, w.dt, sp, w.windows, precision=R.RAD_FP64, box_L=w.L,
+                     options={"defer": 1}) as r:
+        for _ in range(2):
+            r.accumulate_steps(0, X, U)
+            a = r.finalize()
+            b = r.finalize()
+            for g, e, o in zip(a, b, ref[False]):
+                np.testing.assert_array_equal(g, e)
+                if np.any(o):
+                    assert relL2(g, o) <= 1e-10
+            r.reset()
+
+
+def test_error_codes(two_species):
+    R = _rad()
+    w, X, U, _ = two_species
+    sp = [(s[0], s[1], s[2]) for s in w.species]
+    with R.Radiation(w.dirs, w.grids, w.dt, sp, w.windows, precision=R.RAD_FP64, box_L=w.L) as r:
+        with pytest.raises(R.RadError) as ei:
+            r.accumulate(1, X[1], U[1])
+        assert ei.value.code == -4
+        r.accumulate_steps(0, X[:10], U[:10])
+        with pytest.raises(R.RadError) as ei:
+            r.finalize()
+        assert ei.value.code == -5
+        with pytest.raises(R.RadError) as ei:
+            r.set_options(anchor_K=4)
+        assert ei.value.code in (-1, -8)
+    with pytest.raises(R.RadError) as ei:
+        R.Radiation(w.dirs, w.grids, -1.0, sp, w.windows)
+    assert ei.value.code == -1
+    with pytest.raises(R.RadError):
+        R.Radiation(w.dirs, w.grids, w.dt, sp, [(5, 3, 1, 0)])
+    with pytest.raises(R.RadError):
+        R.Radiation(w.dirs, w.grids, w.dt, sp, [(0, 3, 1, 7)])
+    with pytest.raises(R.RadError):
+        R.Radiation(np.zeros((1, 3)), w.grids, w.dt, sp, [(0, 3, 1, 0)])
+
+
+def test_check_inputs_flags_nan(two_species):
+    R = _rad()
+    w, X, U, _ = two_species
+    sp = [(s[0], s[1], s[2]) for s in w.species]
+    Xb = X.copy()
+    Xb[5, 1, 3] = np.nan
+    with R.Radiation(w.dirs, w.grids, w.dt, sp, w.windows, precision=R.RAD_FP32_SPLIT,
+                     box_L=w.L, options={"check_inputs": 1}) as r:
+        r.accumulate_steps(0, Xb, U)
+        with pytest.raises(R.RadError) as ei:
+            r.finalize()
+        assert ei.value.code == -7
+
+
+def test_workload1_full_fp64_and_fp32():
+    """1024 e-, 2000 samples, n = y, 256 log-spaced omega in [0.1, 300]."""
+    R = _rad()
+    w = trajgen.config(1)
+    X, U = w.trajectory_numpy()
+    ref = oracle.spectra(X, U, w.dt, w.dirs, w.grids, w.windows,
+                         [(s[0], s[1]) for s in w.species], box_L=w.L)
+    f64 = _run(w, X, U, R.RAD_FP64)
+    f32 = _run(w, X, U, R.RAD_FP32_SPLIT)
+    assert relL2(f64[0], ref[0]) <= 1e-10
+    assert relL2(f32[0], ref[0]) <= 1e-4
