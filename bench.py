@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Throughput of the in-situ radiation-spectrum hot path on GB300.
+
+One step = one whole pass of the hot path over one batch of synthetic input:
+reset, ingest of every PIC call of the window (leapfrog states already
+resident in HBM), the FP32 split-phase accumulation of the Lienard-Wiechert
+far-field amplitude for every particle x sample x direction x frequency, the
+window-close particle reduction and the finalize, through the C ABI.
+
+Workload (65,536 electrons, gamma 3 two-beam load in a 64-mode static field,
+4096 samples, 8 observer directions, 1024 log-spaced omega in [0.1, 1000]):
+the largest of the five workloads whose inputs fit in HBM at once.  The
+metric is particle.sample.omega.direction updates per second; the FP32 split
+path's error against the FP64 GPU path is measured on a particle subset.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+N > 1 runs under torchrun, one rank per GPU, each on its own particle shard
+(weak scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "G particle·step·ω·n updates/s, FP32 split vs FP64 GPU at ≤1e-4 rel L2"
+UNIT = "G updates/s"
+WORKLOAD = 2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-particles", type=int, default=2048)
+    ap.add_argument("--cpu-particles", type=int, default=96)
+    ap.add_argument("--particles", type=int, default=None,
+                    help="scale the workload to this many particles (profiling cases)")
+    ap.add_argument("--variant", type=int, default=None)
+    ap.add_argument("--anchor-K", type=int, default=None)
+    ap.add_argument("--freq-per-lane", type=int, default=None)
+    return ap.parse_args()
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def workload_config(w, extra=None):
+    cfg = {"workload": f"{w.n_total} e- gamma 3 two-beam, {w.windows[0][1] - w.windows[0][0]} "
+                       f"samples, {len(w.dirs)} dirs, {len(w.grids[0])} log omega "
+                       f"[{w.grids[0][0]:g}, {w.grids[0][-1]:g}]",
+           "particles": w.n_total, "samples": w.windows[0][1] - w.windows[0][0],
+           "directions": len(w.dirs), "omegas": len(w.grids[0]), "dt": w.dt,
+           "path": "FP32 split-phase (FP64 anchor)", "mode": "incoherent",
+           "l2": "inputs larger than L2 (trajectory FP64 in HBM)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_sample(n_particles: int):
+    """Time the FP64 CPU oracle on the first n_particles of the workload."""
+    import numpy as np
+    import oracle
+    import trajgen
+    w = trajgen.config(WORKLOAD)
+    X, U = w.trajectory_numpy(0, n_particles)
+    sp = [(n_particles, w.species[0][1])]
+    t0 = time.perf_counter()
+    oracle.spectra(X, U, w.dt, w.dirs, w.grids, w.windows, sp, box_L=w.L)
+    el = time.perf_counter() - t0
+    s0, s1 = w.windows[0][0], w.windows[0][1]
+    upd = n_particles * (s1 - s0) * len(w.dirs) * len(w.grids[0])
+    return upd, el, oracle.num_threads(), w
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    vals = []
+    for i in range(args.warmup + args.steps):
+        upd, el, cores, w = oracle_sample(args.cpu_particles)
+        if i >= args.warmup:
+            vals.append((upd, el))
+    upd = sum(v[0] for v in vals)
+    el = sum(v[1] for v in vals)
+    value = upd / el / 1e9
+    sample = (f"{args.cpu_particles} of {w.n_total} particles, all samples/directions/omegas "
+              f"({vals[0][0]:.3e} updates per step)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(w, {"path": "FP64 CPU oracle (C, libm, OpenMP)"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200",
+                                       "-i", str(gpu_index)], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for ln in fh:
+                parts = [x.strip() for x in ln.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2])
+                          if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import trajgen
+    from trajgen import gpu as tg
+    import paper_1003_1140_gb300 as R
+    from paper_1003_1140_gb300 import roofline
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = trajgen.config(WORKLOAD)
+    if args.particles:
+        w = trajgen.config(WORKLOAD, args.particles / w.n_total)
+    N = w.n_total
+    # weak scaling: each rank owns its own particle shard of the same size
+    X, U = tg.trajectory_gpu(w, first=rank * N, count=N)
+    sp = [(s[0], s[1], s[2]) for s in w.species]
+    opts = {}
+    if args.variant is not None:
+        opts["variant"] = args.variant
+    if args.anchor_K is not None:
+        opts["anchor_K"] = args.anchor_K
+    if args.freq_per_lane is not None:
+        opts["freq_per_lane"] = args.freq_per_lane
+    ctx = R.Radiation(w.dirs, w.grids, w.dt, sp, w.windows, precision=R.RAD_FP32_SPLIT,
+                      box_L=w.L, options=opts or None)
+    out = torch.empty(ctx.spectrum_size(), dtype=torch.float64, device="cuda")
+    upd = ctx.updates()
+
+    def step():
+        ctx.reset()
+        ctx.accumulate_steps(0, X, U)
+        ctx.finalize(out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    t_before = ctx.timing()
+    barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    st = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    t_after = ctx.timing()
+    acc_ms = t_after["accum_ms"] - t_before["accum_ms"]
+    acc_n = t_after["accum_launches"] - t_before["accum_launches"]
+    ing_n = t_after["ingest_launches"] - t_before["ingest_launches"]
+    launches = int(acc_n + ing_n + args.steps)        # + one finalize kernel per step
+    ms_step = ms / args.steps
+    value = world * upd / (ms_step * 1e-3) / 1e9
+    opts_used = ctx.options()
+
+    # roofline of the dominant kernel (window accumulation), measured live
+    sm_mhz = clocks["sm_mhz"] if clocks else None
+    rl = roofline.accum32_roofline(upd * args.steps / max(acc_n, 1), acc_ms / max(acc_n, 1),
+                                   torch.cuda.get_device_properties(local).multi_processor_count,
+                                   sm_mhz, opts_used)
+
+    # end to end through the public API with host buffers (pinned), H2D/D2H inside
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.empty(X.shape, dtype=torch.float64, pin_memory=True)
+        Uh = torch.empty(U.shape, dtype=torch.float64, pin_memory=True)
+        Xh.copy_(X)
+        Uh.copy_(U)
+        outh = np.empty(ctx.spectrum_size())
+
+        def step_e2e():
+            ctx.reset()
+            ctx.accumulate_steps(0, Xh, Uh)
+            ctx.finalize(outh)
+
+        step_e2e()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        ke = max(1, min(args.steps, 3))
+        for _ in range(ke):
+            step_e2e()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * upd / (el / ke) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(Xh.numel() * 8 + Uh.numel() * 8),
+               "d2h_bytes_per_step": int(outh.size * 8)}
+        del Xh, Uh
+
+    # FP64 GPU path on a particle subset, and the FP32 split error against it
+    n64 = min(args.fp64_particles, N)
+    Xs = X[:, :, :n64].contiguous()
+    Us = U[:, :, :n64].contiguous()
+    c64 = R.Radiation(w.dirs, w.grids, w.dt, [(n64, sp[0][1], sp[0][2])], w.windows,
+                      precision=R.RAD_FP64, box_L=w.L)
+    c64.accumulate_steps(0, Xs, Us)
+    S64 = c64.finalize()[0]
+    t64 = c64.timing()
+    upd64 = c64.updates()
+    c64.close()
+    c32 = R.Radiation(w.dirs, w.grids, w.dt, [(n64, sp[0][1], sp[0][2])], w.windows,
+                      precision=R.RAD_FP32_SPLIT, box_L=w.L, options=opts or None)
+    c32.accumulate_steps(0, Xs, Us)
+    S32 = c32.finalize()[0]
+    c32.close()
+    rel = np.linalg.norm(S32 - S64, axis=1) / np.linalg.norm(S64, axis=1)
+    fp64_rate = upd64 / (t64["accum_ms"] * 1e-3) / 1e9
+    fp32_kernel_rate = upd / (acc_ms / max(acc_n, 1) * 1e-3) / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        cupd, cel, cores, _ = oracle_sample(args.cpu_particles)
+        cpu = {"value": cupd / cel / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"first {args.cpu_particles} particles of the workload, all 4096 "
+                         f"samples x 8 dirs x 1024 omega ({cupd:.3e} updates, {cel:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": workload_config(w, {"options": opts_used,
+                                              "parallelism": f"particle shards x{world}"}),
+                "clocks": clocks, "gpu_launches": launches, "roofline": rl,
+                "e2e": e2e, "cpu_baseline": cpu,
+                "fp64_gpu": {"value": fp64_rate, "unit": UNIT,
+                             "sample": f"{n64} particles, same samples/dirs/omegas"},
+                "fp32_vs_fp64_rel_l2": {"max": float(rel.max()), "per_direction":
+                                        [float(v) for v in rel], "particles": n64},
+                "fp32_kernel_speedup_vs_fp64_gpu": fp32_kernel_rate / fp64_rate}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -67,7 +67,7 @@ extern "C" {
 /* sincos engine of the FP32 split path */
 #define RAD_VARIANT_AUTO 0   /* autotuned (or the cached choice) */
 #define RAD_VARIANT_SFU 1    /* every e^{i theta} by the special-function unit */
-#define RAD_VARIANT_MIX 2    /* part of the frequencies by an FMA-pipe polynomial */
+#define RAD_VARIANT_MIX 2    /* 1 of 4 frequencies by an FMA-pipe polynomial */
 
 typedef struct rad_ctx rad_ctx;
 
@@ -97,7 +97,8 @@ typedef struct {
                               finalize instead of when its last sample arrives */
     int32_t use_graph;     /* 1: replay each step's work as a CUDA graph        */
     int32_t check_inputs;  /* 1: flag non-finite x/u (RAD_ENAN at finalize)    */
-    int32_t mix_sfu_of_16; /* MIX variant: frequencies (of every 16) on the SFU */
+    int32_t blocks_per_sm; /* 0 (auto), 2 or 3: resident blocks per SM the FP32
+                              kernel is built for (its register budget)    */
     int32_t reserved[9];
 } rad_options;
 
@@ -166,8 +167,9 @@ int64_t rad_updates(const rad_ctx *ctx);
 
 /*
  * rad_timing -- device time (CUDA events on the context's stream) spent since
- * init/reset in the window accumulation kernels and in the per-step ingest,
- * and the number of accumulation launches.  Synchronises the stream.
+ * rad_init in the window accumulation kernels and (when enabled) in the
+ * per-step ingest, and the number of accumulation and ingest launches.
+ * rad_reset does not clear these totals.  Synchronises the stream.
  */
 int rad_timing(rad_ctx *ctx, double *accum_ms, double *ingest_ms, int64_t *accum_launches,
                int64_t *ingest_launches);

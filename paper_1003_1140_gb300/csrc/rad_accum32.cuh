@@ -1,4 +1,5 @@
-// rad_accum32.cu -- FP32 split-phase accumulation of the far-field amplitude.
+// rad_accum32.cuh -- FP32 split-phase accumulation of the far-field amplitude
+// (kernel template; instantiated by rad_accum32_*.cu).
 //
 // For every work item (window, direction n, frequency tile, run of particle
 // tiles) the block evaluates, for each particle j and frequency w_k,
@@ -21,16 +22,53 @@
 //   modulo one turn exactly.  dphi_m = (m - a - (K-1)) dt - n.(r_m - r_a) is
 //   formed in FP64 from the ring's FP32 offsets and rounded once, so the
 //   per-update phase is one FP32 FMA: theta = fma(w_k, dphi_m, Theta_k).
-// * e^{i theta} by the special-function unit (__sincosf), 4 FFMA accumulate.
-// * Trajectory chunks (32 samples x 10 components x 8 particles) are staged
-//   into shared memory by TMA (cp.async.bulk.tensor) from a dedicated
-//   producer warp, double-buffered on mbarriers; each compute warp owns one
-//   particle, each lane FT frequencies (stride 32 for coalesced output).
+// * e^{i theta}: by the special-function unit (__sincosf) for the first FT-NP
+//   frequencies of each thread; for the last NP (MIX variant) by an FMA-pipe
+//   polynomial -- Cody-Waite reduction of theta/2 by multiples of pi, minimax
+//   sin (degree 9) and cos (degree 8) on [-pi/2, pi/2], double angle -- so
+//   both the MUFU and the FMA pipes carry the transcendental work.
+// * The trajectory ring is tile-major ([tile][slot][comp][8 particles]), so a
+//   chunk of 32 samples x 10 components x 8 particles is one contiguous 10 KB
+//   block, staged into shared memory by a bulk TMA copy (cp.async.bulk) from a
+//   dedicated producer warp, double-buffered on mbarriers.  Each compute warp
+//   owns one particle; each lane FT frequencies (stride 32: coalesced output).
 // * Persistent grid: block b takes items b, b + gridDim.x, ... from a list
 //   sorted by decreasing cost.
+#pragma once
+
 #include "rad_internal.cuh"
 
 namespace rad {
+
+// FMA-pipe e^{i theta} constants (fit_sincos.py: minimax on [-pi/2, pi/2]).
+constexpr float kS3 = -1.666665673e-01f, kS5 = 8.333017118e-03f, kS7 = -1.980661473e-04f,
+                kS9 = 2.600054813e-06f;
+constexpr float kC2 = -4.999993145e-01f, kC4 = 4.166398942e-02f, kC6 = -1.385592739e-03f,
+                kC8 = 2.319438681e-05f;
+constexpr float kPiHi = 3.141592741e+00f, kPiLo = -8.742277657e-08f;
+constexpr float kInvPi = 0.318309886183790671538f;
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: x + kMagic - kMagic = rint(x)
+
+// cos(2 h) and sin(2 h) / 2 for the half angle h (|h| < 2^22 pi).
+__device__ __forceinline__ void poly_cis_half(float h, float& c2, float& s2half)
+{
+    const float t = fmaf(h, kInvPi, kMagic);
+    const float k = t - kMagic;
+    float y = fmaf(k, -kPiHi, h);
+    y = fmaf(k, -kPiLo, y);
+    const float y2 = y * y;
+    float p = fmaf(y2, kS9, kS7);
+    p = fmaf(y2, p, kS5);
+    p = fmaf(y2, p, kS3);
+    const float y3 = y * y2;
+    const float s = fmaf(y3, p, y);
+    float q = fmaf(y2, kC8, kC6);
+    q = fmaf(y2, q, kC4);
+    q = fmaf(y2, q, kC2);
+    const float c = fmaf(y2, q, 1.0f);
+    c2 = fmaf(c, c, -(s * s));
+    s2half = c * s;
+}
 
 // Constants of the work item every compute warp is on; kept in shared memory
 // (re-read where used) so that the update loop holds only its accumulators.
@@ -41,32 +79,39 @@ struct ItemSmem {
     float n[3], e1[3], e2[3];
     float qdt;
     int32_t grid_off, grid_len;
-    int32_t col0, count, tile0, ntiles, ftile, dir;
+    int32_t count, tile0, ntiles, ftile, dir, tilebase;
 };
 
 template <int FT, int K, bool COH>
 struct Smem32 {
-    float tbuf[2][kChunk32][kComps][kTileP];   // 2 x 10240 B, TMA destinations
+    float tbuf[2][kChunk32][kComps][kTileP];   // 2 x 10240 B, bulk-copy destinations
     float4 geo[kComputeWarps][kChunk32];        // V1, V2, dphi per sample
     float2 anc[kComputeWarps][kChunk32 / K];    // phi_ref as hi + lo
-    float ths[kComputeWarps][kChunk32 / K][FT][32];  // anchor phases Theta per block
+    float ths[kComputeWarps][kChunk32 / K][FT][32];  // anchor phases per block
     float red[kComputeWarps][FT][32];           // window-close partials
     double run[(COH ? 4 : 1) * FT * 32];        // per-item particle sums (FP64)
-    ItemSmem item;                              // the current item's constants
+    ItemSmem item;
     uint64_t full[2];
     uint64_t empty[2];
     int abort_flag;
 };
 
-template <int FT, int K, bool COH>
-__global__ void __launch_bounds__(kBlockThreads, 2)
-    accum32_kernel(const __grid_constant__ CUtensorMap tmap, const Accum32Params p)
+template <int FT, int NP, int K, bool COH>
+constexpr size_t smem32_bytes()
 {
+    return sizeof(Smem32<FT, K, COH>) + 128;
+}
+
+template <int FT, int NP, int K, bool COH, int MB>
+__global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum32Params p)
+{
+    static_assert(NP >= 0 && NP < FT, "polynomial frequencies per thread");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     auto& S = *reinterpret_cast<Smem32<FT, K, COH>*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     constexpr uint32_t kBytes = sizeof(S.tbuf[0]);
     constexpr int kNRun = (COH ? 4 : 1) * FT * 32;
+    constexpr int NS = FT - NP;   // SFU frequencies per thread
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
@@ -92,17 +137,18 @@ __global__ void __launch_bounds__(kBlockThreads, 2)
             const WorkItem it = p.items[ii];
             const WinDev w = p.wins[it.win];
             const int64_t c0 = w.s0 / kChunk32, c1 = (w.s1 - 1) / kChunk32;
-            const int32_t colbase = p.species[it.sp].col0;
+            const int64_t tilebase = p.species[it.sp].col0 / kTileP;
             for (int t = 0; t < it.ntiles; ++t) {
-                const int col = colbase + (it.tile0 + t) * kTileP;
+                const int64_t tile = tilebase + it.tile0 + t;
                 for (int64_t c = c0; c <= c1; ++c, ++L) {
                     const int buf = L & 1;
                     if (L >= 2) mbar_wait_bounded(&S.empty[buf], ((L - 2) >> 1) & 1, abort_flag,
                                                   p.err_word);
                     if (*abort_flag) continue;
                     mbar_arrive_expect_tx(&S.full[buf], kBytes);
-                    const int z = (int)((c * kChunk32) % p.ring);
-                    tma_load_3d(&S.tbuf[buf][0][0][0], &tmap, col, 0, z, &S.full[buf]);
+                    const int64_t slot = (c * kChunk32) % p.ring;
+                    const float* src = p.slab32 + (tile * p.ring + slot) * (kComps * kTileP);
+                    bulk_load(&S.tbuf[buf][0][0][0], src, kBytes, &S.full[buf]);
                 }
             }
         }
@@ -134,20 +180,21 @@ __global__ void __launch_bounds__(kBlockThreads, 2)
             I.qdt = (float)spd.qdt;
             I.grid_off = w.grid_off;
             I.grid_len = w.grid_len;
-            I.col0 = spd.col0;
             I.count = spd.count;
             I.tile0 = it.tile0;
             I.ntiles = it.ntiles;
             I.ftile = it.ftile;
             I.dir = it.dir;
+            I.tilebase = spd.col0 / kTileP;
         }
         named_barrier_sync(1, kComputeWarps * 32);
         const int kbase = S.item.ftile * (32 * FT) + lane;
-        float om[FT];
+        float om[FT];   // omega (SFU) or omega / 2 (polynomial)
 #pragma unroll
         for (int i = 0; i < FT; ++i) {
             const int k = kbase + 32 * i;
-            om[i] = (k < S.item.grid_len) ? p.omega[S.item.grid_off + k] : 0.0f;
+            const float wk = (k < S.item.grid_len) ? p.omega[S.item.grid_off + k] : 0.0f;
+            om[i] = (i < NS) ? wk : 0.5f * wk;
         }
         const int ntiles = S.item.ntiles;
 
@@ -164,16 +211,15 @@ __global__ void __launch_bounds__(kBlockThreads, 2)
                 {
                     const ItemSmem& I = S.item;
                     const float* tb = &S.tbuf[buf][lane][0][warp];
-                    const float dr0 = tb[0 * kTileP], dr1 = tb[1 * kTileP], dr2 = tb[2 * kTileP];
                     const float b0 = tb[3 * kTileP], b1 = tb[4 * kTileP], b2 = tb[5 * kTileP];
-                    const float d0 = tb[6 * kTileP], d1 = tb[7 * kTileP], d2 = tb[8 * kTileP];
-                    const float g = tb[9 * kTileP];
                     const float bn = I.n[0] * b0 + I.n[1] * b1 + I.n[2] * b2;
                     const float p1 = I.e1[0] * b0 + I.e1[1] * b1 + I.e1[2] * b2;
                     const float p2 = I.e2[0] * b0 + I.e2[1] * b1 + I.e2[2] * b2;
+                    const float d0 = tb[6 * kTileP], d1 = tb[7 * kTileP], d2 = tb[8 * kTileP];
                     const float dn = I.n[0] * d0 + I.n[1] * d1 + I.n[2] * d2;
                     const float q1 = I.e1[0] * d0 + I.e1[1] * d1 + I.e1[2] * d2;
                     const float q2 = I.e2[0] * d0 + I.e2[1] * d1 + I.e2[2] * d2;
+                    const float g = tb[9 * kTileP];
                     const float kap = bn > 0.0f ? (g + p1 * p1 + p2 * p2) / (1.0f + bn) : 1.0f - bn;
                     const float inv = I.qdt / (kap * kap);
                     const float V1 = -(p1 * dn + q1 * kap) * inv;
@@ -181,11 +227,11 @@ __global__ void __launch_bounds__(kBlockThreads, 2)
                     const int64_t m = c * kChunk32 + lane;
                     const int64_t a = m - (m & (K - 1));
                     const double dphi = (double)(m - a - (K - 1)) * p.dt -
-                                        (I.nd[0] * (double)dr0 + I.nd[1] * (double)dr1 +
-                                         I.nd[2] * (double)dr2);
+                                        (I.nd[0] * (double)tb[0] + I.nd[1] * (double)tb[kTileP] +
+                                         I.nd[2] * (double)tb[2 * kTileP]);
                     S.geo[warp][lane] = make_float4(V1, V2, (float)dphi, 0.0f);
                     if ((lane & (K - 1)) == 0) {
-                        const int64_t col = I.col0 + (int64_t)(I.tile0 + t) * kTileP + warp;
+                        const int64_t col = (int64_t)(I.tilebase + I.tile0 + t) * kTileP + warp;
                         const int64_t blk = (a / K) % p.nblk;
                         const double* ra = p.anchors + blk * 3 * p.ncols + col;
                         const double phi_ref = (double)(a + K - 1) * p.dt -
@@ -200,7 +246,8 @@ __global__ void __launch_bounds__(kBlockThreads, 2)
                 if (lane == 0) mbar_arrive(&S.empty[buf]);
 
                 // ---- anchor phases Theta_k = 2 pi frac(nu_k phi_ref) of the chunk's
-                // anchor blocks (float-float product, exact reduction to one turn)
+                // anchor blocks (float-float product, exact reduction to one turn);
+                // halved for the polynomial frequencies
                 const int64_t cs = c * kChunk32;
                 const int lo = (int)((S.item.s0 > cs ? S.item.s0 : cs) - cs);
                 const int hi = (int)((S.item.s1 < cs + kChunk32 ? S.item.s1 : cs + kChunk32) - cs);
@@ -217,28 +264,49 @@ __global__ void __launch_bounds__(kBlockThreads, 2)
                         const float pe = fmaf(nh, an.x, -pr);
                         const float tl = fmaf(nl, an.x, fmaf(nh, an.y, pe));
                         const float fr = pr - rintf(pr);
-                        S.ths[warp][b][i][lane] = (fr + tl) * 6.28318530717958647f;
+                        S.ths[warp][b][i][lane] =
+                            (fr + tl) * (i < NS ? 6.28318530717958647f : 3.14159265358979323f);
                     }
                 }
                 __syncwarp();
 
-                // ---- update loop over the chunk's samples inside the window
+                // ---- update loop over the chunk's samples inside the window, one
+                // anchor block at a time; the next sample's geometry is loaded
+                // while the current one is being accumulated
 #pragma unroll 1
-                for (int l = lo; l < hi; ++l) {
-                    if (l == lo || (l & (K - 1)) == 0) {
+                for (int b = lo / K; b * K < hi; ++b) {
+                    const int l0 = lo > b * K ? lo : b * K;
+                    const int l1 = hi < b * K + K ? hi : b * K + K;
 #pragma unroll
-                        for (int i = 0; i < FT; ++i) th[i] = S.ths[warp][l / K][i][lane];
-                    }
-                    const float4 gg = S.geo[warp][l];
+                    for (int i = 0; i < FT; ++i) th[i] = S.ths[warp][b][i][lane];
+                    float4 gg = S.geo[warp][l0];
+#pragma unroll 1
+                    for (int l = l0; l < l1; ++l) {
+                        const float4 gn = S.geo[warp][(l + 1) & (kChunk32 - 1)];
 #pragma unroll
-                    for (int i = 0; i < FT; ++i) {
-                        const float tt = fmaf(om[i], gg.z, th[i]);
-                        float sn, cs_;
-                        __sincosf(tt, &sn, &cs_);
-                        a1r[i] = fmaf(gg.x, cs_, a1r[i]);
-                        a1i[i] = fmaf(gg.x, sn, a1i[i]);
-                        a2r[i] = fmaf(gg.y, cs_, a2r[i]);
-                        a2i[i] = fmaf(gg.y, sn, a2i[i]);
+                        for (int i = 0; i < NS; ++i) {
+                            const float tt = fmaf(om[i], gg.z, th[i]);
+                            float sn, cs_;
+                            __sincosf(tt, &sn, &cs_);
+                            a1r[i] = fmaf(gg.x, cs_, a1r[i]);
+                            a1i[i] = fmaf(gg.x, sn, a1i[i]);
+                            a2r[i] = fmaf(gg.y, cs_, a2r[i]);
+                            a2i[i] = fmaf(gg.y, sn, a2i[i]);
+                        }
+                        if (NP > 0) {
+                            const float v1d = gg.x + gg.x, v2d = gg.y + gg.y;
+#pragma unroll
+                            for (int i = NS; i < FT; ++i) {
+                                const float hh = fmaf(om[i], gg.z, th[i]);
+                                float cs_, snh;
+                                poly_cis_half(hh, cs_, snh);
+                                a1r[i] = fmaf(gg.x, cs_, a1r[i]);
+                                a1i[i] = fmaf(v1d, snh, a1i[i]);
+                                a2r[i] = fmaf(gg.y, cs_, a2r[i]);
+                                a2i[i] = fmaf(v2d, snh, a2i[i]);
+                            }
+                        }
+                        gg = gn;
                     }
                 }
                 __syncwarp();
@@ -311,54 +379,39 @@ __global__ void __launch_bounds__(kBlockThreads, 2)
     }
 }
 
-template <int FT, int K, bool COH>
-static cudaError_t launch_one(const CUtensorMap& tmap, const Accum32Params& p, int grid,
-                              cudaStream_t st)
+template <int FT, int NP, int K, bool COH, int MB>
+cudaError_t launch32_one(const Accum32Params& p, int grid, cudaStream_t st)
 {
-    auto kern = accum32_kernel<FT, K, COH>;
-    const size_t smem = sizeof(Smem32<FT, K, COH>) + 128;
+    auto kern = accum32_kernel<FT, NP, K, COH, MB>;
+    const size_t smem = smem32_bytes<FT, NP, K, COH>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, kBlockThreads, smem, st>>>(tmap, p);
+    kern<<<grid, kBlockThreads, smem, st>>>(p);
     return cudaGetLastError();
 }
 
-template <int FT, int K, bool COH>
-static int blocks_per_sm_one()
+template <int FT, int NP, int K, bool COH, int MB>
+int blocks32_one()
 {
     int nb = 0;
-    const size_t smem = sizeof(Smem32<FT, K, COH>) + 128;
-    cudaFuncSetAttribute(accum32_kernel<FT, K, COH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, accum32_kernel<FT, K, COH>, kBlockThreads,
-                                                  smem);
+    const size_t smem = smem32_bytes<FT, NP, K, COH>();
+    if (cudaFuncSetAttribute(accum32_kernel<FT, NP, K, COH, MB>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, accum32_kernel<FT, NP, K, COH, MB>,
+                                                      kBlockThreads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     return nb;
 }
 
-#define RAD_DISPATCH32(FN, ...)                                                   \
-    do {                                                                          \
-        if (ft == 8) {                                                            \
-            if (K == 8) { if (coh) return FN<8, 8, true>(__VA_ARGS__); else return FN<8, 8, false>(__VA_ARGS__); } \
-            if (K == 16) { if (coh) return FN<8, 16, true>(__VA_ARGS__); else return FN<8, 16, false>(__VA_ARGS__); } \
-            if (coh) return FN<8, 32, true>(__VA_ARGS__); else return FN<8, 32, false>(__VA_ARGS__); \
-        } else {                                                                  \
-            if (K == 8) { if (coh) return FN<16, 8, true>(__VA_ARGS__); else return FN<16, 8, false>(__VA_ARGS__); } \
-            if (K == 16) { if (coh) return FN<16, 16, true>(__VA_ARGS__); else return FN<16, 16, false>(__VA_ARGS__); } \
-            if (coh) return FN<16, 32, true>(__VA_ARGS__); else return FN<16, 32, false>(__VA_ARGS__); \
-        }                                                                         \
-    } while (0)
-
-cudaError_t launch_accum32(const CUtensorMap& tmap, const Accum32Params& p, int ft, int K,
-                           bool coh, int grid, cudaStream_t st)
-{
-    if (p.n_items == 0) return cudaSuccess;
-    RAD_DISPATCH32(launch_one, tmap, p, grid, st);
-}
-
-int accum32_blocks_per_sm(int ft, int K, bool coh)
-{
-    RAD_DISPATCH32(blocks_per_sm_one);
-}
+// One instantiation family: (FT, NP, MB) for every K and both summation modes.
+#define RAD_ACCUM32_FAMILY(FT, NP, MB)                                                       \
+    if (cfg.ft == FT && cfg.np == NP && cfg.mb == MB) {                                      \
+        if (cfg.K == 8) { if (cfg.coh) FN(FT, NP, 8, true, MB); else FN(FT, NP, 8, false, MB); } \
+        if (cfg.K == 16) { if (cfg.coh) FN(FT, NP, 16, true, MB); else FN(FT, NP, 16, false, MB); } \
+        if (cfg.K == 32) { if (cfg.coh) FN(FT, NP, 32, true, MB); else FN(FT, NP, 32, false, MB); } \
+    }
 
 }  // namespace rad

@@ -6,7 +6,8 @@
 // double-precision sincos, FP64 accumulators and FP64 particle sums.  This is
 // the GPU reference against which the FP32 split path is judged; on GB300 it
 // is bound by the FP64 pipe.  Trajectory chunks (16 samples x 10 components
-// x 8 particles, FP64) are TMA-staged exactly as in the FP32 path.
+// x 8 particles, FP64; one contiguous 10 KB block of the tile-major ring) are
+// staged by bulk TMA copies exactly as in the FP32 path.
 #include "rad_internal.cuh"
 
 namespace rad {
@@ -24,7 +25,7 @@ struct Smem64 {
 
 template <int FT, bool COH>
 __global__ void __launch_bounds__(kBlockThreads, 1)
-    accum64_kernel(const __grid_constant__ CUtensorMap tmap, const Accum64Params p)
+    accum64_kernel(const Accum64Params p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     auto& S = *reinterpret_cast<Smem64<FT, COH>*>(
@@ -54,17 +55,18 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
             const WorkItem it = p.items[ii];
             const WinDev w = p.wins[it.win];
             const int64_t c0 = w.s0 / kChunk64, c1 = (w.s1 - 1) / kChunk64;
-            const int32_t colbase = p.species[it.sp].col0;
+            const int64_t tilebase = p.species[it.sp].col0 / kTileP;
             for (int t = 0; t < it.ntiles; ++t) {
-                const int col = colbase + (it.tile0 + t) * kTileP;
+                const int64_t tile = tilebase + it.tile0 + t;
                 for (int64_t c = c0; c <= c1; ++c, ++L) {
                     const int buf = L & 1;
                     if (L >= 2) mbar_wait_bounded(&S.empty[buf], ((L - 2) >> 1) & 1, abort_flag,
                                                   p.err_word);
                     if (*abort_flag) continue;
                     mbar_arrive_expect_tx(&S.full[buf], kBytes);
-                    const int z = (int)((c * kChunk64) % p.ring);
-                    tma_load_3d(&S.tbuf[buf][0][0][0], &tmap, col, 0, z, &S.full[buf]);
+                    const int64_t slot = (c * kChunk64) % p.ring;
+                    const double* src = p.slab64 + (tile * p.ring + slot) * (kComps * kTileP);
+                    bulk_load(&S.tbuf[buf][0][0][0], src, kBytes, &S.full[buf]);
                 }
             }
         }
@@ -201,15 +203,14 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
 }
 
 template <int FT, bool COH>
-static cudaError_t launch64_one(const CUtensorMap& tmap, const Accum64Params& p, int grid,
-                                cudaStream_t st)
+static cudaError_t launch64_one(const Accum64Params& p, int grid, cudaStream_t st)
 {
     auto kern = accum64_kernel<FT, COH>;
     const size_t smem = sizeof(Smem64<FT, COH>) + 128;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, kBlockThreads, smem, st>>>(tmap, p);
+    kern<<<grid, kBlockThreads, smem, st>>>(p);
     return cudaGetLastError();
 }
 
@@ -227,12 +228,10 @@ static int blocks64_one()
 
 constexpr int kFT64 = 4;
 
-cudaError_t launch_accum64(const CUtensorMap& tmap, const Accum64Params& p, bool coh, int grid,
-                           cudaStream_t st)
+cudaError_t launch_accum64(const Accum64Params& p, bool coh, int grid, cudaStream_t st)
 {
     if (p.n_items == 0) return cudaSuccess;
-    return coh ? launch64_one<kFT64, true>(tmap, p, grid, st)
-               : launch64_one<kFT64, false>(tmap, p, grid, st);
+    return coh ? launch64_one<kFT64, true>(p, grid, st) : launch64_one<kFT64, false>(p, grid, st);
 }
 
 int accum64_blocks_per_sm(bool coh)

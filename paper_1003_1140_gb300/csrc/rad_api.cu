@@ -14,8 +14,6 @@
 #include <string>
 #include <vector>
 
-#include <cudaTypedefs.h>
-
 #include "rad.h"
 #include "rad_internal.cuh"
 
@@ -44,7 +42,8 @@ struct rad_ctx {
     std::vector<int64_t> out_off;
     int64_t out_len = 0;
     rad_options opt{};
-    int ft = 16, K = 16;
+    Accum32Config cfg{8, 0, 16, false, 2};
+    int K = 16;                    // anchor interval used by the ingest
     bool frozen = false;           // options frozen after the first step
 
     // device / stream
@@ -61,7 +60,6 @@ struct rad_ctx {
     double* x_prev = nullptr;
     double* r_prev = nullptr;
     double* u_prev = nullptr;
-    CUtensorMap tmap{};
 
     // tables
     float* d_dirs32 = nullptr;
@@ -171,27 +169,18 @@ static void basis(const double n[3], double e1[3], double e2[3])
     e2[2] = n[0] * e1[1] - n[1] * e1[0];
 }
 
-static PFN_cuTensorMapEncodeTiled_v12000 get_encode()
+bool rad::accum32_dispatch(const Accum32Params* p, const Accum32Config& cfg, int grid,
+                           cudaStream_t st, cudaError_t* err, int* nb)
 {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                             cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-        else
-            cudaGetLastError();
-    }
-    return fn;
+    return accum32_ft8_sfu(p, cfg, grid, st, err, nb) || accum32_ft8_mix(p, cfg, grid, st, err, nb) ||
+           accum32_ft16(p, cfg, grid, st, err, nb);
 }
 
 static int chunk_len(const rad_ctx* c) { return c->precision == RAD_FP64 ? kChunk64 : kChunk32; }
 
 static int freq_tile(const rad_ctx* c)
 {
-    return c->precision == RAD_FP64 ? 32 * accum64_ft() : 32 * c->ft;
+    return c->precision == RAD_FP64 ? 32 * accum64_ft() : 32 * c->cfg.ft;
 }
 
 // Build the work items of one event (set of windows) and sort by cost.
@@ -240,7 +229,10 @@ static void build_items(rad_ctx* c, Event& ev, int total_blocks)
 static int blocks_per_sm(const rad_ctx* c)
 {
     if (c->precision == RAD_FP64) return std::max(1, accum64_blocks_per_sm(c->mode == RAD_COHERENT));
-    return std::max(1, accum32_blocks_per_sm(c->ft, c->K, c->mode == RAD_COHERENT));
+    int nb = 0;
+    cudaError_t e = cudaSuccess;
+    if (!accum32_dispatch(nullptr, c->cfg, 0, nullptr, &e, &nb)) return 0;
+    return nb;
 }
 
 static cudaEvent_t next_event(std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& pool, size_t& used,
@@ -265,9 +257,13 @@ static int freeze(rad_ctx* c)
     CU(cudaSetDevice(c->device));
     if (c->precision == RAD_FP32_SPLIT) {
         c->K = c->opt.anchor_K ? c->opt.anchor_K : 16;
-        int maxlen = 1;
-        for (int g = 0; g < c->n_grids; ++g) maxlen = std::max(maxlen, c->grid_len[g]);
-        c->ft = c->opt.freq_per_lane ? c->opt.freq_per_lane : (maxlen <= 256 ? 8 : 16);
+        c->cfg.K = c->K;
+        c->cfg.ft = c->opt.freq_per_lane ? c->opt.freq_per_lane : 8;
+        c->cfg.np = c->opt.variant == RAD_VARIANT_MIX ? (c->cfg.ft == 8 ? 2 : 4) : 0;
+        c->cfg.coh = c->mode == RAD_COHERENT;
+        c->cfg.mb = c->opt.blocks_per_sm ? c->opt.blocks_per_sm : 2;
+        if (c->cfg.ft == 16 && c->cfg.mb != 2)
+            return fail(c, RAD_EINVAL, "16 frequencies per thread is built for 2 blocks per SM only");
         // anchor positions: one FP64 3-vector per particle per K samples of the ring
         c->nblk = c->ring / c->K;
         if (!c->anchors) {
@@ -295,7 +291,9 @@ static int freeze(rad_ctx* c)
             c->events.push_back(ev);
         }
     }
-    const int total_blocks = blocks_per_sm(c) * c->sms;
+    const int bps = blocks_per_sm(c);
+    if (bps < 1) return fail(c, RAD_EINVAL, "the selected kernel variant cannot be resident");
+    const int total_blocks = bps * c->sms;
     for (auto& ev : c->events) {
         build_items(c, ev, total_blocks);
         if (!ev.items.empty()) {
@@ -304,21 +302,6 @@ static int freeze(rad_ctx* c)
                           cudaMemcpyHostToDevice));
         }
     }
-    // TMA descriptor over the ring
-    auto enc = get_encode();
-    if (!enc) return fail(c, RAD_ECUDA, "cuTensorMapEncodeTiled is not available");
-    const bool f64 = c->precision == RAD_FP64;
-    const size_t es = f64 ? 8 : 4;
-    cuuint64_t dims[3] = {(cuuint64_t)c->ncols, (cuuint64_t)kComps, (cuuint64_t)c->ring};
-    cuuint64_t strides[2] = {(cuuint64_t)(c->ncols * es), (cuuint64_t)(c->ncols * es * kComps)};
-    cuuint32_t box[3] = {(cuuint32_t)kTileP, (cuuint32_t)kComps, (cuuint32_t)chunk_len(c)};
-    cuuint32_t estr[3] = {1, 1, 1};
-    void* base = f64 ? (void*)c->slab64 : (void*)c->slab32;
-    CUresult r = enc(&c->tmap, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                     3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(c, RAD_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     c->frozen = true;
     return RAD_OK;
 }
@@ -339,11 +322,12 @@ static int launch_event(rad_ctx* c, Event& ev)
         p.species = c->d_species;
         p.dirs64 = c->d_dirs64;
         p.omega = c->d_om64;
+        p.slab64 = c->slab64;
         p.ring = c->ring;
         p.dt = c->dt;
         p.acc = c->acc;
         p.err_word = c->d_err;
-        e = launch_accum64(c->tmap, p, c->mode == RAD_COHERENT, grid, c->stream);
+        e = launch_accum64(p, c->mode == RAD_COHERENT, grid, c->stream);
     } else {
         Accum32Params p{};
         p.items = ev.d_items;
@@ -355,6 +339,7 @@ static int launch_event(rad_ctx* c, Event& ev)
         p.omega = c->d_om32;
         p.nu_hi = c->d_nuhi;
         p.nu_lo = c->d_nulo;
+        p.slab32 = c->slab32;
         p.anchors = c->anchors;
         p.ncols = c->ncols;
         p.ring = c->ring;
@@ -362,7 +347,9 @@ static int launch_event(rad_ctx* c, Event& ev)
         p.dt = c->dt;
         p.acc = c->acc;
         p.err_word = c->d_err;
-        e = launch_accum32(c->tmap, p, c->ft, c->K, c->mode == RAD_COHERENT, grid, c->stream);
+        e = cudaSuccess;
+        if (!accum32_dispatch(&p, c->cfg, grid, c->stream, &e, nullptr))
+            return fail(c, RAD_EINVAL, "kernel variant not built");
     }
     if (e != cudaSuccess) return fail(c, RAD_ECUDA, "accumulation launch failed: %s", cudaGetErrorString(e));
     cudaEvent_t e1 = next_event(c->acc_ev, c->acc_used, false);
@@ -613,8 +600,8 @@ int rad_set_options(rad_ctx* c, const rad_options* o)
         return fail(c, RAD_EINVAL, "anchor_K must be 0, 8, 16 or 32");
     if (o->freq_per_lane != 0 && o->freq_per_lane != 8 && o->freq_per_lane != 16)
         return fail(c, RAD_EINVAL, "freq_per_lane must be 0, 8 or 16");
-    if (o->mix_sfu_of_16 < 0 || o->mix_sfu_of_16 > 16)
-        return fail(c, RAD_EINVAL, "mix_sfu_of_16 must be in [0, 16]");
+    if (o->blocks_per_sm != 0 && o->blocks_per_sm != 2 && o->blocks_per_sm != 3)
+        return fail(c, RAD_EINVAL, "blocks_per_sm must be 0, 2 or 3");
     c->opt = *o;
     c->time_ingest = o->reserved[0] != 0;
     return RAD_OK;
@@ -625,9 +612,10 @@ int rad_get_options(const rad_ctx* c, rad_options* o)
     if (!c || !o) return RAD_EINVAL;
     *o = c->opt;
     if (c->frozen && c->precision == RAD_FP32_SPLIT) {
-        o->anchor_K = c->K;
-        o->freq_per_lane = c->ft;
-        if (o->variant == RAD_VARIANT_AUTO) o->variant = RAD_VARIANT_SFU;
+        o->anchor_K = c->cfg.K;
+        o->freq_per_lane = c->cfg.ft;
+        o->blocks_per_sm = c->cfg.mb;
+        o->variant = c->cfg.np > 0 ? RAD_VARIANT_MIX : RAD_VARIANT_SFU;
     }
     return RAD_OK;
 }
@@ -734,8 +722,6 @@ int rad_reset(rad_ctx* c)
     CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
     c->next_step = 0;
     c->deferred_done = false;
-    c->acc_used = c->ing_used = 0;
-    c->acc_launches = c->ing_launches = 0;
     return RAD_OK;
 }
 

@@ -5,7 +5,7 @@
 // the samples the accumulation needs, one call late: sample m = s - 1 uses
 //   r_m       = unwrapped x_m (minimum image in a periodic box),
 //   beta_m    = ubar / sqrt(1 + ubar^2),  ubar = (u_{m-1/2} + u_{m+1/2}) / 2,
-//   betadot_m = (beta_{m+1/2} - beta_{m-1/2}) / dt   (FP64, before rounding),
+//   betadot_m = (beta_{m+1/2} - beta_{m-1/2}) / dt,
 //   g_m       = 1/gamma_m^2 = 1 / (1 + ubar^2).
 // One thread per particle walks the launch's steps in order, keeping the
 // previous raw position, the unwrapped position and u_{s-3/2} in registers
@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestParams p)
     while (sp + 1 < p.n_species && i >= p.in_off[sp + 1]) ++sp;
     const int64_t col = p.col_off[sp] + (i - p.in_off[sp]);
     const int64_t nc = p.ncols;
+    const int64_t tile = col / kTileP, pp = col % kTileP;
 
     double xp[3], rp[3], up[3], ra[3];
     bool have_state = p.step0 > 0;
@@ -65,21 +66,14 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestParams p)
 
         // sample m = s - 1: r_m = rp, u_{m-1/2} = up, u_{m+1/2} = un
         const int64_t m = s - 1;
-        double ub[3];
-        for (int c = 0; c < 3; ++c) ub[c] = 0.5 * (up[c] + un[c]);
-        const double gm = sqrt(1.0 + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
-        const double gp = sqrt(1.0 + (un[0] * un[0] + un[1] * un[1] + un[2] * un[2]));
-        const double gb2 = 1.0 + (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
-        const double gb = sqrt(gb2);
-        double beta[3], bdot[3];
-        for (int c = 0; c < 3; ++c) {
-            beta[c] = ub[c] / gb;
-            bdot[c] = (un[c] / gp - up[c] / gm) / p.dt;
-        }
-        const double g = 1.0 / gb2;
         const int64_t slot = m % p.ring;
-
         if (p.slab32) {
+            // FP32 ring: the only cancellation-prone quantities are differenced
+            // in FP64 -- du = u_{m+1/2} - u_{m-1/2} and r_m - r_anchor -- and the
+            // rest is evaluated in FP32 through the rearrangement
+            //   beta_+ - beta_- = du/g_+ - u_- (du.(u_+ + u_-)) / (g_+ g_- (g_+ + g_-)),
+            // which has no cancellation for the magnetic (du perpendicular to u)
+            // and weakly parallel accelerations a frozen-field push produces.
             if ((m % p.K) == 0) {
                 const int64_t blk = (m / p.K) % p.nblk;
                 for (int c = 0; c < 3; ++c) {
@@ -92,29 +86,49 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestParams p)
                 for (int c = 0; c < 3; ++c) ra[c] = p.anchors[(blk * 3 + c) * nc + col];
                 have_anchor = true;
             }
-            float* o = p.slab32 + slot * kComps * nc + col;
-            o[0 * nc] = (float)(rp[0] - ra[0]);
-            o[1 * nc] = (float)(rp[1] - ra[1]);
-            o[2 * nc] = (float)(rp[2] - ra[2]);
-            o[3 * nc] = (float)beta[0];
-            o[4 * nc] = (float)beta[1];
-            o[5 * nc] = (float)beta[2];
-            o[6 * nc] = (float)bdot[0];
-            o[7 * nc] = (float)bdot[1];
-            o[8 * nc] = (float)bdot[2];
-            o[9 * nc] = (float)g;
+            float um[3], uq[3], du[3], ub[3];
+            for (int c = 0; c < 3; ++c) {
+                um[c] = (float)up[c];
+                uq[c] = (float)un[c];
+                du[c] = (float)(un[c] - up[c]);
+                ub[c] = 0.5f * (um[c] + uq[c]);
+            }
+            const float gm = sqrtf(1.0f + (um[0] * um[0] + um[1] * um[1] + um[2] * um[2]));
+            const float gq = sqrtf(1.0f + (uq[0] * uq[0] + uq[1] * uq[1] + uq[2] * uq[2]));
+            const float gb2 = 1.0f + (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
+            const float igb = rsqrtf(gb2);
+            const float dus = du[0] * (uq[0] + um[0]) + du[1] * (uq[1] + um[1]) +
+                              du[2] * (uq[2] + um[2]);
+            const float igq = 1.0f / gq;
+            const float corr = dus / (gq * gm * (gq + gm));
+            const float idt = (float)(1.0 / p.dt);
+            float* o = p.slab32 + (tile * p.ring + slot) * (kComps * kTileP) + pp;
+            o[0 * kTileP] = (float)(rp[0] - ra[0]);
+            o[1 * kTileP] = (float)(rp[1] - ra[1]);
+            o[2 * kTileP] = (float)(rp[2] - ra[2]);
+            o[3 * kTileP] = ub[0] * igb;
+            o[4 * kTileP] = ub[1] * igb;
+            o[5 * kTileP] = ub[2] * igb;
+            o[6 * kTileP] = (du[0] * igq - um[0] * corr) * idt;
+            o[7 * kTileP] = (du[1] * igq - um[1] * corr) * idt;
+            o[8 * kTileP] = (du[2] * igq - um[2] * corr) * idt;
+            o[9 * kTileP] = 1.0f / gb2;
         } else {
-            double* o = p.slab64 + slot * kComps * nc + col;
-            o[0 * nc] = rp[0];
-            o[1 * nc] = rp[1];
-            o[2 * nc] = rp[2];
-            o[3 * nc] = beta[0];
-            o[4 * nc] = beta[1];
-            o[5 * nc] = beta[2];
-            o[6 * nc] = bdot[0];
-            o[7 * nc] = bdot[1];
-            o[8 * nc] = bdot[2];
-            o[9 * nc] = g;
+            double ub[3];
+            for (int c = 0; c < 3; ++c) ub[c] = 0.5 * (up[c] + un[c]);
+            const double gm = sqrt(1.0 + (up[0] * up[0] + up[1] * up[1] + up[2] * up[2]));
+            const double gp = sqrt(1.0 + (un[0] * un[0] + un[1] * un[1] + un[2] * un[2]));
+            const double gb2 = 1.0 + (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
+            const double gb = sqrt(gb2);
+            double* o = p.slab64 + (tile * p.ring + slot) * (kComps * kTileP) + pp;
+            o[0 * kTileP] = rp[0];
+            o[1 * kTileP] = rp[1];
+            o[2 * kTileP] = rp[2];
+            for (int c = 0; c < 3; ++c) {
+                o[(3 + c) * kTileP] = ub[c] / gb;
+                o[(6 + c) * kTileP] = (un[c] / gp - up[c] / gm) / p.dt;
+            }
+            o[9 * kTileP] = 1.0 / gb2;
         }
         for (int c = 0; c < 3; ++c) {
             xp[c] = xn[c];

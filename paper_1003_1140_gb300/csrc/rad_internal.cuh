@@ -11,13 +11,16 @@ namespace rad {
 // ---------------------------------------------------------------------------
 // trajectory ring layout
 // ---------------------------------------------------------------------------
-// FP32 split path: slab[slot][c][col] float, c = 0..9 =
+// Both rings are tile-major: element (tile, slot, c, p) of particle column
+// col = 8 tile + p sits at ((tile * ring + slot) * 10 + c) * 8 + p, so the
+// chunk of consecutive slots the kernels stage is one contiguous block.
+// FP32 split path: slab[tile][slot][c][p] float, c = 0..9 =
 //   dr (3)   : r_m - r_a, the offset from the block's FP64 anchor position
 //   beta (3) : beta_m
 //   bdot (3) : betadot_m (differenced in FP64 before the rounding)
 //   g (1)    : 1/gamma_m^2 = 1/(1 + ubar^2)
 // anchors[blk][c][col] double: r_a at samples a = K * blk (ring of blocks).
-// FP64 path: slab64[slot][c][col] double with c = r (3, absolute unwrapped),
+// FP64 path: slab64[tile][slot][c][p] double with c = r (3, absolute unwrapped),
 // beta (3), bdot (3), g (1).
 constexpr int kComps = 10;
 constexpr int kTileP = 8;      // particles per tile: one warp each
@@ -126,14 +129,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return false;
 }
 
-// 3-D tiled TMA load of one box into shared memory, completion on `bar`.
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y,
-                                            int z, uint64_t* bar)
+// 1-D bulk copy (TMA) of `bytes` contiguous bytes into shared memory,
+// completion on `bar`.  Both addresses 16-byte aligned, bytes % 16 == 0.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar)
 {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_addr(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_addr(bar)), "r"(x), "r"(y), "r"(z)
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes),
+        "r"(smem_addr(bar))
         : "memory");
 }
 
@@ -181,6 +185,7 @@ struct Accum32Params {
     const float* omega;       // [n_freq] rad per unit time
     const float* nu_hi;       // [n_freq] (omega / 2 pi) hi part
     const float* nu_lo;       // [n_freq] lo part
+    const float* slab32;      // tile-major FP32 ring
     const double* anchors;    // [nblk][3][ncols]
     int64_t ncols;
     int64_t ring;
@@ -197,6 +202,7 @@ struct Accum64Params {
     const SpeciesDev* species;
     const double* dirs64;     // [D][9]: n, e1, e2
     const double* omega;      // [n_freq]
+    const double* slab64;     // tile-major FP64 ring
     int64_t ring;
     double dt;
     double* acc;
@@ -204,11 +210,23 @@ struct Accum64Params {
 };
 
 cudaError_t launch_ingest(const IngestParams& p, cudaStream_t st);
-cudaError_t launch_accum32(const CUtensorMap& tmap, const Accum32Params& p, int ft, int K,
-                           bool coh, int grid, cudaStream_t st);
-int accum32_blocks_per_sm(int ft, int K, bool coh);
-cudaError_t launch_accum64(const CUtensorMap& tmap, const Accum64Params& p, bool coh, int grid,
-                           cudaStream_t st);
+// FP32 kernel variant: frequencies per thread, of which np by the FMA-pipe
+// polynomial, anchor interval K, coherent sum, minimum resident blocks per SM.
+struct Accum32Config {
+    int ft, np, K;
+    bool coh;
+    int mb;
+};
+bool accum32_ft8_sfu(const Accum32Params* p, const Accum32Config& cfg, int grid,
+                     cudaStream_t st, cudaError_t* err, int* nb);
+bool accum32_ft8_mix(const Accum32Params* p, const Accum32Config& cfg, int grid,
+                     cudaStream_t st, cudaError_t* err, int* nb);
+bool accum32_ft16(const Accum32Params* p, const Accum32Config& cfg, int grid,
+                  cudaStream_t st, cudaError_t* err, int* nb);
+// launch (p != nullptr) or occupancy query; false if the variant is not built
+bool accum32_dispatch(const Accum32Params* p, const Accum32Config& cfg, int grid,
+                      cudaStream_t st, cudaError_t* err, int* nb);
+cudaError_t launch_accum64(const Accum64Params& p, bool coh, int grid, cudaStream_t st);
 int accum64_blocks_per_sm(bool coh);
 int accum64_ft();
 

@@ -62,7 +62,7 @@ class rad_options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("anchor_K", ctypes.c_int32),
                 ("freq_per_lane", ctypes.c_int32), ("defer", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("check_inputs", ctypes.c_int32),
-                ("mix_sfu_of_16", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
 
 
 _lock = threading.Lock()

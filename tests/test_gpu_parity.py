@@ -96,11 +96,17 @@ def test_fp32_split_matches_oracle(two_species, coherent, K):
     _check(got, ref[coherent], 1e-4, per_direction=True)
 
 
-def test_fp32_split_sixteen_freq_per_lane(two_species):
+@pytest.mark.parametrize("variant,ft,mb", [(1, 16, 2), (1, 8, 3), (2, 8, 2), (2, 8, 3),
+                                           (2, 16, 2)])
+@pytest.mark.parametrize("coherent", [False, True])
+def test_fp32_split_kernel_variants(two_species, variant, ft, mb, coherent):
+    """SFU-only and SFU + FMA-polynomial (MIX) kernels, 8 or 16 frequencies per
+    thread, built for 2 or 3 resident blocks per SM."""
     R = _rad()
     w, X, U, ref = two_species
-    got = _run(w, X, U, R.RAD_FP32_SPLIT, options={"freq_per_lane": 16})
-    _check(got, ref[False], 1e-4, per_direction=True)
+    got = _run(w, X, U, R.RAD_FP32_SPLIT, coherent,
+               options={"variant": variant, "freq_per_lane": ft, "blocks_per_sm": mb})
+    _check(got, ref[coherent], 1e-4, per_direction=True)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
