@@ -15,13 +15,16 @@
 //   kappa = 1 - n.beta evaluated as (g + (e1.beta)^2 + (e2.beta)^2)/(1 + n.beta)
 //   when n.beta > 0 (no cancellation at high gamma), else directly.
 //   |A|^2 = |A.e1|^2 + |A.e2|^2: two complex accumulators per (j, n, w).
-// * Phase split: phi_m = phi_ref + dphi_m.  phi_ref is the FP64 retarded time
-//   at the block's anchor sample a = K floor(m/K), shifted to the middle of the
-//   block's phase range; it enters once per K samples through the float-float
-//   product nu_k * phi_ref (nu = w / 2 pi, both as hi+lo FP32 pairs) reduced
-//   modulo one turn exactly.  dphi_m = (m - a - (K-1)) dt - n.(r_m - r_a) is
-//   formed in FP64 from the ring's FP32 offsets and rounded once, so the
-//   per-update phase is one FP32 FMA: theta = fma(w_k, dphi_m, Theta_k).
+// * Phase split: phi_m = phi_ref + dphi_m.  phi_ref is the retarded time at
+//   the block's anchor sample a = K floor(m/K), shifted to the middle of the
+//   block's phase range, carried as a float-float (hi + lo FP32) pair with
+//   FP64-class accuracy; it enters once per K samples through the float-float
+//   product nu_k * phi_ref (nu = w / 2 pi) reduced modulo one turn exactly.
+//   dphi_m = (m - a - (K-1)) dt - n.(r_m - r_a) is formed with compensated
+//   (error-free) FP32 arithmetic from the ring's FP32 offsets and rounded
+//   once, so the per-update phase is one FP32 FMA:
+//   theta = fma(w_k, dphi_m, Theta_k).  GB300's FP64 pipe is 1/64 of FP32
+//   and its latency stalls the warps, so the kernel issues no FP64 at all.
 // * e^{i theta}: by the special-function unit (__sincosf) for the first FT-NP
 //   frequencies of each thread; for the last NP (MIX variant) by an FMA-pipe
 //   polynomial -- Cody-Waite reduction of theta/2 by multiples of pi, minimax
@@ -29,11 +32,16 @@
 //   both the MUFU and the FMA pipes carry the transcendental work.
 // * The trajectory ring is tile-major ([tile][slot][comp][8 particles]), so a
 //   chunk of 32 samples x 10 components x 8 particles is one contiguous 10 KB
-//   block, staged into shared memory by a bulk TMA copy (cp.async.bulk) from a
-//   dedicated producer warp, double-buffered on mbarriers.  Each compute warp
-//   owns one particle; each lane FT frequencies (stride 32: coalesced output).
-// * Persistent grid: block b takes items b, b + gridDim.x, ... from a list
-//   sorted by decreasing cost.
+//   block (its anchor positions another), staged into shared memory by bulk
+//   TMA copies (cp.async.bulk).  Warp specialisation: a producer warp issues
+//   the copies and turns each chunk into geometry and anchor phases in shared
+//   memory (double-buffered, mbarrier hand-off); eight compute warps run only
+//   the update loop, one particle per warp, FT frequencies per lane (stride
+//   32: coalesced output).
+// * Persistent grid with a dynamic longest-first schedule: the producer of each
+//   block takes the next item of a list sorted by decreasing cost from an atomic
+//   counter and describes every chunk it hands over (item, tile, sample range,
+//   first/last flags), so the compute warps need no schedule of their own.
 #pragma once
 
 #include "rad_internal.cuh"
@@ -70,37 +78,82 @@ __device__ __forceinline__ void poly_cis_half(float h, float& c2, float& s2half)
     s2half = c * s;
 }
 
-// Constants of the work item every compute warp is on; kept in shared memory
-// (re-read where used) so that the update loop holds only its accumulators.
-struct ItemSmem {
-    double nd[3];          // n (FP64) for the phase offsets
-    int64_t s0, s1;        // window
-    int64_t out_off;
-    float n[3], e1[3], e2[3];
-    float qdt;
-    int32_t grid_off, grid_len;
-    int32_t count, tile0, ntiles, ftile, dir, tilebase;
+// What the producer tells the compute warps about the chunk in a buffer.
+struct ChunkMeta {
+    int64_t out_off;       // the item's output block
+    int32_t ii;            // item index (-1: no more work)
+    int32_t lo, hi;        // samples [lo, hi) of the chunk inside the window
+    int32_t flags;         // kFirstOfTile | kLastOfTile | kFirstOfItem | kLastOfItem
+    int32_t real;          // particles of this tile that exist (0..8)
+    int32_t grid_len, ftile, dir;
 };
+constexpr int kFirstOfTile = 1, kLastOfTile = 2, kFirstOfItem = 4, kLastOfItem = 8;
 
 template <int FT, int K, bool COH>
 struct Smem32 {
-    float tbuf[2][kChunk32][kComps][kTileP];   // 2 x 10240 B, bulk-copy destinations
-    float4 geo[kComputeWarps][kChunk32];        // V1, V2, dphi per sample
-    float2 anc[kComputeWarps][kChunk32 / K];    // phi_ref as hi + lo
-    float ths[kComputeWarps][kChunk32 / K][FT][32];  // anchor phases per block
-    float red[kComputeWarps][FT][32];           // window-close partials
-    double run[(COH ? 4 : 1) * FT * 32];        // per-item particle sums (FP64)
-    ItemSmem item;
-    uint64_t full[2];
-    uint64_t empty[2];
+    float tbuf[2][kChunk32][kComps][kTileP];          // bulk-copy destinations (producer only)
+    float tanc[2][kChunk32 / K][6][kTileP];           // the chunk's anchor positions (hi, lo)
+    float4 geo[2][kComputeWarps][kChunk32 + 1];       // V1, V2, dphi per particle and sample
+    float ths[2][kComputeWarps][kChunk32 / K][FT][32];  // anchor phases per particle, block
+    float2 anc[kComputeWarps][kChunk32 / K];          // phi_ref (hi, lo) of the current chunk
+    float red[kComputeWarps][FT][32];                 // window-close partials
+    double run[(COH ? 4 : 1) * FT * 32];              // per-item particle sums (FP64)
+    ChunkMeta meta[2];
+    uint64_t tfull[2];                                // bulk copy landed
+    uint64_t gfull[2];                                // geometry of a chunk ready
+    uint64_t gempty[2];                               // compute warps done with a chunk
+    uint64_t cbar;                                    // compute-warp barrier (bounded)
     int abort_flag;
 };
+
+// Barrier among the compute warps with a bounded wait: unlike bar.sync it
+// cannot hang if a warp has left after a device-side timeout.
+__device__ __forceinline__ void compute_sync(uint64_t* bar, uint32_t& phase, int lane,
+                                             volatile int* abort_flag, int* err_word)
+{
+    __syncwarp();
+    if (lane == 0) mbar_arrive(bar);
+    mbar_wait_bounded(bar, phase & 1, abort_flag, err_word);
+    ++phase;
+}
 
 template <int FT, int NP, int K, bool COH>
 constexpr size_t smem32_bytes()
 {
     return sizeof(Smem32<FT, K, COH>) + 128;
 }
+
+// The producer's walk over (item, tile, chunk): items come from an atomic
+// counter (items are sorted by decreasing cost, so this is a dynamic
+// longest-first schedule); every tile of an item; every 32-sample chunk the
+// item's window touches.  All lanes of the producer warp hold the same state.
+struct ChunkCursor {
+    int ii, t, ntiles;
+    int64_t c, c0, c1;
+    bool valid;
+    __device__ void load_item(const Accum32Params& p, int lane)
+    {
+        int v = 0;
+        if (lane == 0) v = atomicAdd(p.counter, 1);
+        ii = __shfl_sync(0xffffffffu, v, 0);
+        valid = ii < p.n_items;
+        if (!valid) return;
+        const WorkItem it = p.items[ii];
+        const WinDev w = p.wins[it.win];
+        ntiles = it.ntiles;
+        c0 = w.s0 / kChunk32;
+        c1 = (w.s1 - 1) / kChunk32;
+        t = 0;
+        c = c0;
+    }
+    __device__ void next(const Accum32Params& p, int lane)
+    {
+        if (++c <= c1) return;
+        c = c0;
+        if (++t < ntiles) return;
+        load_item(p, lane);
+    }
+};
 
 template <int FT, int NP, int K, bool COH, int MB>
 __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum32Params p)
@@ -118,10 +171,12 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
     const int lane = tid & 31;
 
     if (tid == 0) {
-        mbar_init(&S.full[0], 1);
-        mbar_init(&S.full[1], 1);
-        mbar_init(&S.empty[0], kComputeWarps);
-        mbar_init(&S.empty[1], kComputeWarps);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&S.tfull[b], 1);
+            mbar_init(&S.gfull[b], 1);
+            mbar_init(&S.gempty[b], kComputeWarps);
+        }
+        mbar_init(&S.cbar, kComputeWarps);
         S.abort_flag = 0;
         fence_mbar_init();
     }
@@ -129,191 +184,271 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
     __syncthreads();
     volatile int* abort_flag = &S.abort_flag;
 
-    // ------------------------------------------------------------------ producer
+    // ---------------------------------------------------------------- producer
+    // Lane 0 streams the chunks (samples and anchor positions) in with bulk
+    // copies one chunk ahead; the whole warp turns each landed chunk into the
+    // per-sample geometry (V1, V2, dphi) and the per-anchor-block phases Theta
+    // of the 8 particles, for the compute warps.  FP32 only: the quantities
+    // that need FP64 accuracy use float-float (error-free) arithmetic.
     if (warp == kComputeWarps) {
-        if (lane != 0) return;
+        constexpr int NB = kChunk32 / K;                      // anchor blocks per chunk
+        constexpr uint32_t kAncBytes = sizeof(S.tanc[0]);
+        // cur is the chunk being turned into geometry; nxt, one chunk ahead, is
+        // the only cursor that advances (and so the only one that takes items
+        // from the counter): each item is fetched exactly once.
+        ChunkCursor cur;
+        cur.load_item(p, lane);
+        bool pending[2] = {false, false};     // copy issued, not yet seen landed
+        uint32_t pend_parity[2] = {0, 0};
+        uint32_t uses[2] = {0, 0};            // copies issued into each buffer
+        auto issue = [&](const ChunkCursor& q, int buf) {
+            if (lane == 0 && !*abort_flag) {
+                pending[buf] = true;
+                pend_parity[buf] = uses[buf] & 1;
+                const WorkItem it = p.items[q.ii];
+                const int64_t tile = p.species[it.sp].col0 / kTileP + it.tile0 + q.t;
+                const int64_t slot = (q.c * kChunk32) % p.ring;
+                const int64_t blk = (q.c * NB) % p.nblk;
+                const float* src = p.slab32 + (tile * p.ring + slot) * (kComps * kTileP);
+                const float* asrc = p.anc32 + (tile * p.nblk + blk) * (6 * kTileP);
+                fence_proxy_async();
+                mbar_arrive_expect_tx(&S.tfull[buf], kBytes + kAncBytes);
+                bulk_load(&S.tbuf[buf][0][0][0], src, kBytes, &S.tfull[buf]);
+                bulk_load(&S.tanc[buf][0][0][0], asrc, kAncBytes, &S.tfull[buf]);
+            }
+            ++uses[buf];
+        };
+        if (cur.valid) issue(cur, 0);
+        int item_loaded = -1;
+        float nuh[FT], nul[FT];
+        float n0 = 0, n1 = 0, n2 = 0, e10 = 0, e11 = 0, e12 = 0, e20 = 0, e21 = 0, e22 = 0;
+        float nl0 = 0, nl1 = 0, nl2 = 0, qdt = 0;
+        int64_t s0 = 0, s1 = 0, out_off = 0;
+        int grid_len = 0, ftile = 0, dir = 0, count = 0, tile0 = 0;
         uint32_t L = 0;
-        for (int ii = blockIdx.x; ii < p.n_items; ii += gridDim.x) {
-            const WorkItem it = p.items[ii];
-            const WinDev w = p.wins[it.win];
-            const int64_t c0 = w.s0 / kChunk32, c1 = (w.s1 - 1) / kChunk32;
-            const int64_t tilebase = p.species[it.sp].col0 / kTileP;
-            for (int t = 0; t < it.ntiles; ++t) {
-                const int64_t tile = tilebase + it.tile0 + t;
-                for (int64_t c = c0; c <= c1; ++c, ++L) {
-                    const int buf = L & 1;
-                    if (L >= 2) mbar_wait_bounded(&S.empty[buf], ((L - 2) >> 1) & 1, abort_flag,
-                                                  p.err_word);
-                    if (*abort_flag) continue;
-                    mbar_arrive_expect_tx(&S.full[buf], kBytes);
-                    const int64_t slot = (c * kChunk32) % p.ring;
-                    const float* src = p.slab32 + (tile * p.ring + slot) * (kComps * kTileP);
-                    bulk_load(&S.tbuf[buf][0][0][0], src, kBytes, &S.full[buf]);
+        for (; cur.valid; ++L) {
+            const int buf = L & 1;
+            ChunkCursor nxt = cur;
+            nxt.next(p, lane);
+            if (nxt.valid) issue(nxt, buf ^ 1);   // chunk L+1 into the other buffer
+            if (cur.ii != item_loaded) {
+                item_loaded = cur.ii;
+                const WorkItem it = p.items[cur.ii];
+                const WinDev w = p.wins[it.win];
+                const float* dv = p.dirs32 + 12 * it.dir;
+                n0 = dv[0]; n1 = dv[1]; n2 = dv[2];
+                e10 = dv[3]; e11 = dv[4]; e12 = dv[5];
+                e20 = dv[6]; e21 = dv[7]; e22 = dv[8];
+                nl0 = dv[9]; nl1 = dv[10]; nl2 = dv[11];
+                qdt = (float)p.species[it.sp].qdt;
+                count = p.species[it.sp].count;
+                s0 = w.s0;
+                s1 = w.s1;
+                out_off = w.out_off;
+                grid_len = w.grid_len;
+                ftile = it.ftile;
+                dir = it.dir;
+                tile0 = it.tile0;
+#pragma unroll
+                for (int i = 0; i < FT; ++i) {
+                    const int k = it.ftile * (32 * FT) + lane + 32 * i;
+                    const int kk = w.grid_off + (k < w.grid_len ? k : 0);
+                    nuh[i] = p.nu_hi[kk];
+                    nul[i] = p.nu_lo[kk];
                 }
             }
-        }
-        // never leave the block with a copy in flight
-        if (L >= 1) mbar_wait_bounded(&S.full[(L - 1) & 1], ((L - 1) >> 1) & 1, abort_flag,
-                                      p.err_word);
-        if (L >= 2) mbar_wait_bounded(&S.full[(L - 2) & 1], ((L - 2) >> 1) & 1, abort_flag,
-                                      p.err_word);
-        return;
-    }
-
-    // ------------------------------------------------------------------ compute
-    uint32_t L = 0;
-    for (int ii = blockIdx.x; ii < p.n_items; ii += gridDim.x) {
-        if (tid == 0) {
-            const WorkItem it = p.items[ii];
-            const WinDev w = p.wins[it.win];
-            const SpeciesDev spd = p.species[it.sp];
-            ItemSmem& I = S.item;
-            for (int q = 0; q < 3; ++q) {
-                I.nd[q] = p.dirs64[3 * it.dir + q];
-                I.n[q] = p.dirs32[9 * it.dir + q];
-                I.e1[q] = p.dirs32[9 * it.dir + 3 + q];
-                I.e2[q] = p.dirs32[9 * it.dir + 6 + q];
-            }
-            I.s0 = w.s0;
-            I.s1 = w.s1;
-            I.out_off = w.out_off;
-            I.qdt = (float)spd.qdt;
-            I.grid_off = w.grid_off;
-            I.grid_len = w.grid_len;
-            I.count = spd.count;
-            I.tile0 = it.tile0;
-            I.ntiles = it.ntiles;
-            I.ftile = it.ftile;
-            I.dir = it.dir;
-            I.tilebase = spd.col0 / kTileP;
-        }
-        named_barrier_sync(1, kComputeWarps * 32);
-        const int kbase = S.item.ftile * (32 * FT) + lane;
-        float om[FT];   // omega (SFU) or omega / 2 (polynomial)
+            if (L >= 2) mbar_wait_bounded(&S.gempty[buf], ((L - 2) >> 1) & 1, abort_flag, p.err_word);
+            if (mbar_wait_bounded(&S.tfull[buf], (L >> 1) & 1, abort_flag, p.err_word))
+                pending[buf] = false;
+            const int64_t c = cur.c;
+            // anchor reference phase of (particle pp, block b):
+            //   phi_ref = (a + K - 1) dt - n . r_a,  a = 32 c + K b   (float-float)
+            if (lane < kTileP * NB) {
+                const int pp = lane & (kTileP - 1), b = lane >> 3;
+                const float ta = (float)(c * kChunk32 + b * K + (K - 1));
+                ff t = two_prod(ta, p.dt_hi);
+                float e = fmaf(ta, p.dt_lo, t.lo);
+                float sh = t.hi;
+                const float nh[3] = {n0, n1, n2}, nlo[3] = {nl0, nl1, nl2};
 #pragma unroll
-        for (int i = 0; i < FT; ++i) {
-            const int k = kbase + 32 * i;
-            const float wk = (k < S.item.grid_len) ? p.omega[S.item.grid_off + k] : 0.0f;
-            om[i] = (i < NS) ? wk : 0.5f * wk;
-        }
-        const int ntiles = S.item.ntiles;
-
-        for (int t = 0; t < ntiles; ++t) {
-            float a1r[FT], a1i[FT], a2r[FT], a2i[FT], th[FT];
-#pragma unroll
-            for (int i = 0; i < FT; ++i) a1r[i] = a1i[i] = a2r[i] = a2i[i] = th[i] = 0.0f;
-            const int64_t c0 = S.item.s0 / kChunk32, c1 = (S.item.s1 - 1) / kChunk32;
-
-            for (int64_t c = c0; c <= c1; ++c, ++L) {
-                const int buf = L & 1;
-                mbar_wait_bounded(&S.full[buf], (L >> 1) & 1, abort_flag, p.err_word);
-                // ---- geometry of sample m = 32 c + lane for this warp's particle
-                {
-                    const ItemSmem& I = S.item;
-                    const float* tb = &S.tbuf[buf][lane][0][warp];
-                    const float b0 = tb[3 * kTileP], b1 = tb[4 * kTileP], b2 = tb[5 * kTileP];
-                    const float bn = I.n[0] * b0 + I.n[1] * b1 + I.n[2] * b2;
-                    const float p1 = I.e1[0] * b0 + I.e1[1] * b1 + I.e1[2] * b2;
-                    const float p2 = I.e2[0] * b0 + I.e2[1] * b1 + I.e2[2] * b2;
-                    const float d0 = tb[6 * kTileP], d1 = tb[7 * kTileP], d2 = tb[8 * kTileP];
-                    const float dn = I.n[0] * d0 + I.n[1] * d1 + I.n[2] * d2;
-                    const float q1 = I.e1[0] * d0 + I.e1[1] * d1 + I.e1[2] * d2;
-                    const float q2 = I.e2[0] * d0 + I.e2[1] * d1 + I.e2[2] * d2;
-                    const float g = tb[9 * kTileP];
-                    const float kap = bn > 0.0f ? (g + p1 * p1 + p2 * p2) / (1.0f + bn) : 1.0f - bn;
-                    const float inv = I.qdt / (kap * kap);
-                    const float V1 = -(p1 * dn + q1 * kap) * inv;
-                    const float V2 = -(p2 * dn + q2 * kap) * inv;
-                    const int64_t m = c * kChunk32 + lane;
-                    const int64_t a = m - (m & (K - 1));
-                    const double dphi = (double)(m - a - (K - 1)) * p.dt -
-                                        (I.nd[0] * (double)tb[0] + I.nd[1] * (double)tb[kTileP] +
-                                         I.nd[2] * (double)tb[2 * kTileP]);
-                    S.geo[warp][lane] = make_float4(V1, V2, (float)dphi, 0.0f);
-                    if ((lane & (K - 1)) == 0) {
-                        const int64_t col = (int64_t)(I.tilebase + I.tile0 + t) * kTileP + warp;
-                        const int64_t blk = (a / K) % p.nblk;
-                        const double* ra = p.anchors + blk * 3 * p.ncols + col;
-                        const double phi_ref = (double)(a + K - 1) * p.dt -
-                                               (I.nd[0] * ra[0] + I.nd[1] * ra[p.ncols] +
-                                                I.nd[2] * ra[2 * p.ncols]);
-                        const float hi = (float)phi_ref;
-                        const float lo = (float)(phi_ref - (double)hi);
-                        S.anc[warp][lane / K] = make_float2(hi, lo);
-                    }
+                for (int q = 0; q < 3; ++q) {
+                    const float rh = S.tanc[buf][b][q][pp], rl = S.tanc[buf][b][3 + q][pp];
+                    const ff d = two_prod(nh[q], rh);
+                    const float dl = fmaf(nh[q], rl, fmaf(nlo[q], rh, d.lo));
+                    const ff u = two_sum(sh, -d.hi);
+                    sh = u.hi;
+                    e = e + (u.lo - dl);
                 }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&S.empty[buf]);
-
-                // ---- anchor phases Theta_k = 2 pi frac(nu_k phi_ref) of the chunk's
-                // anchor blocks (float-float product, exact reduction to one turn);
-                // halved for the polynomial frequencies
-                const int64_t cs = c * kChunk32;
-                const int lo = (int)((S.item.s0 > cs ? S.item.s0 : cs) - cs);
-                const int hi = (int)((S.item.s1 < cs + kChunk32 ? S.item.s1 : cs + kChunk32) - cs);
+                const float hi = sh + e;
+                S.anc[pp][b] = make_float2(hi, e - (hi - sh));
+            }
+            // geometry: round r handles sample 4 r + lane / 8 of particle lane % 8
+#pragma unroll 2
+            for (int r = 0; r < kChunk32 / 4; ++r) {
+                const int sm = 4 * r + (lane >> 3), pp = lane & (kTileP - 1);
+                const float* tb = &S.tbuf[buf][sm][0][pp];
+                const float b0 = tb[3 * kTileP], b1 = tb[4 * kTileP], b2 = tb[5 * kTileP];
+                const float d0 = tb[6 * kTileP], d1 = tb[7 * kTileP], d2 = tb[8 * kTileP];
+                const float g = tb[9 * kTileP];
+                const float bn = n0 * b0 + n1 * b1 + n2 * b2;
+                const float p1 = e10 * b0 + e11 * b1 + e12 * b2;
+                const float p2 = e20 * b0 + e21 * b1 + e22 * b2;
+                const float dn = n0 * d0 + n1 * d1 + n2 * d2;
+                const float q1 = e10 * d0 + e11 * d1 + e12 * d2;
+                const float q2 = e20 * d0 + e21 * d1 + e22 * d2;
+                const float kap = bn > 0.0f ? (g + p1 * p1 + p2 * p2) / (1.0f + bn) : 1.0f - bn;
+                const float inv = qdt / (kap * kap);
+                const float V1 = -(p1 * dn + q1 * kap) * inv;
+                const float V2 = -(p2 * dn + q2 * kap) * inv;
+                // dphi = ((sm mod K) - (K - 1)) dt - n . dr, compensated
+                const float ti = (float)((sm & (K - 1)) - (K - 1));
+                const ff t = two_prod(ti, p.dt_hi);
+                float e = fmaf(ti, p.dt_lo, t.lo);
+                float sh = t.hi;
+                const float dr[3] = {tb[0], tb[kTileP], tb[2 * kTileP]};
+                const float nh[3] = {n0, n1, n2}, nlo[3] = {nl0, nl1, nl2};
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const ff d = two_prod(nh[q], dr[q]);
+                    const float dl = fmaf(nlo[q], dr[q], d.lo);
+                    const ff u = two_sum(sh, -d.hi);
+                    sh = u.hi;
+                    e = e + (u.lo - dl);
+                }
+                S.geo[buf][pp][sm] = make_float4(V1, V2, sh + e, 0.0f);
+            }
+            __syncwarp();
+            // anchor phases Theta_k = 2 pi frac(nu_k phi_ref) (float-float product,
+            // exact reduction to one turn); halved for the polynomial frequencies
+            const int64_t cs = c * kChunk32;
+            const int lo = (int)((s0 > cs ? s0 : cs) - cs);
+            const int hi = (int)((s1 < cs + kChunk32 ? s1 : cs + kChunk32) - cs);
+#pragma unroll 1
+            for (int pp = 0; pp < kTileP; ++pp) {
 #pragma unroll 1
                 for (int b = lo / K; b * K < hi; ++b) {
-                    const float2 an = S.anc[warp][b];
-                    const int goff = S.item.grid_off, glen = S.item.grid_len;
+                    const float2 an = S.anc[pp][b];
 #pragma unroll
                     for (int i = 0; i < FT; ++i) {
-                        const int k = kbase + 32 * i;
-                        const int kk = goff + (k < glen ? k : 0);
-                        const float nh = __ldg(p.nu_hi + kk), nl = __ldg(p.nu_lo + kk);
-                        const float pr = nh * an.x;
-                        const float pe = fmaf(nh, an.x, -pr);
-                        const float tl = fmaf(nl, an.x, fmaf(nh, an.y, pe));
+                        const float pr = nuh[i] * an.x;
+                        const float pe = fmaf(nuh[i], an.x, -pr);
+                        const float tl = fmaf(nul[i], an.x, fmaf(nuh[i], an.y, pe));
                         const float fr = pr - rintf(pr);
-                        S.ths[warp][b][i][lane] =
+                        S.ths[buf][pp][b][i][lane] =
                             (fr + tl) * (i < NS ? 6.28318530717958647f : 3.14159265358979323f);
                     }
                 }
-                __syncwarp();
+            }
+            if (lane == 0) {
+                ChunkMeta& M = S.meta[buf];
+                M.out_off = out_off;
+                M.ii = cur.ii;
+                M.lo = lo;
+                M.hi = hi;
+                M.flags = (c == cur.c0 ? kFirstOfTile : 0) | (c == cur.c1 ? kLastOfTile : 0) |
+                          (c == cur.c0 && cur.t == 0 ? kFirstOfItem : 0) |
+                          (c == cur.c1 && cur.t == cur.ntiles - 1 ? kLastOfItem : 0);
+                const int base = (tile0 + cur.t) * kTileP;
+                M.real = count - base < 0 ? 0 : (count - base > kTileP ? kTileP : count - base);
+                M.grid_len = grid_len;
+                M.ftile = ftile;
+                M.dir = dir;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.gfull[buf]);
+            cur = nxt;
+        }
+        // tell the compute warps there is no more work
+        {
+            const int buf = L & 1;
+            if (L >= 2) mbar_wait_bounded(&S.gempty[buf], ((L - 2) >> 1) & 1, abort_flag, p.err_word);
+            if (lane == 0) {
+                S.meta[buf].ii = -1;
+                mbar_arrive(&S.gfull[buf]);
+            }
+        }
+        // never leave the block with a copy in flight (only possible after an abort)
+        if (lane == 0) {
+            for (int b = 0; b < 2; ++b)
+                if (pending[b]) mbar_drain(&S.tfull[b], pend_parity[b]);
+        }
+        return;
+    }
 
-                // ---- update loop over the chunk's samples inside the window, one
-                // anchor block at a time; the next sample's geometry is loaded
-                // while the current one is being accumulated
+    // ---------------------------------------------------------------- compute
+    float om[FT];   // omega (SFU) or omega / 2 (polynomial)
+    float a1r[FT], a1i[FT], a2r[FT], a2i[FT], th[FT];
+#pragma unroll
+    for (int i = 0; i < FT; ++i) om[i] = a1r[i] = a1i[i] = a2r[i] = a2i[i] = th[i] = 0.0f;
+    uint32_t cphase = 0;
+    for (uint32_t L = 0;; ++L) {
+        const int buf = L & 1;
+        mbar_wait_bounded(&S.gfull[buf], (L >> 1) & 1, abort_flag, p.err_word);
+        const int ii = S.meta[buf].ii;
+        if (ii < 0 || *abort_flag) break;
+        const int flags = S.meta[buf].flags;
+        const int lo = S.meta[buf].lo, hi = S.meta[buf].hi;
+        if (flags & kFirstOfItem) {
+            const WorkItem it = p.items[ii];
+            const WinDev w = p.wins[it.win];
+#pragma unroll
+            for (int i = 0; i < FT; ++i) {
+                const int k = it.ftile * (32 * FT) + lane + 32 * i;
+                const float wk = (k < w.grid_len) ? p.omega[w.grid_off + k] : 0.0f;
+                om[i] = (i < NS) ? wk : 0.5f * wk;
+            }
+        }
+        if (flags & kFirstOfTile) {
+#pragma unroll
+            for (int i = 0; i < FT; ++i) a1r[i] = a1i[i] = a2r[i] = a2i[i] = 0.0f;
+        }
+        // update loop, one anchor block at a time; the next sample's geometry
+        // is loaded while the current one is accumulated
 #pragma unroll 1
-                for (int b = lo / K; b * K < hi; ++b) {
-                    const int l0 = lo > b * K ? lo : b * K;
-                    const int l1 = hi < b * K + K ? hi : b * K + K;
+        for (int b = lo / K; b * K < hi; ++b) {
+            const int l0 = lo > b * K ? lo : b * K;
+            const int l1 = hi < b * K + K ? hi : b * K + K;
 #pragma unroll
-                    for (int i = 0; i < FT; ++i) th[i] = S.ths[warp][b][i][lane];
-                    float4 gg = S.geo[warp][l0];
+            for (int i = 0; i < FT; ++i) th[i] = S.ths[buf][warp][b][i][lane];
+            float4 gg = S.geo[buf][warp][l0];
 #pragma unroll 1
-                    for (int l = l0; l < l1; ++l) {
-                        const float4 gn = S.geo[warp][(l + 1) & (kChunk32 - 1)];
+            for (int l = l0; l < l1; ++l) {
+                const float4 gn = S.geo[buf][warp][(l + 1) & (kChunk32 - 1)];
 #pragma unroll
-                        for (int i = 0; i < NS; ++i) {
-                            const float tt = fmaf(om[i], gg.z, th[i]);
-                            float sn, cs_;
-                            __sincosf(tt, &sn, &cs_);
-                            a1r[i] = fmaf(gg.x, cs_, a1r[i]);
-                            a1i[i] = fmaf(gg.x, sn, a1i[i]);
-                            a2r[i] = fmaf(gg.y, cs_, a2r[i]);
-                            a2i[i] = fmaf(gg.y, sn, a2i[i]);
-                        }
-                        if (NP > 0) {
-                            const float v1d = gg.x + gg.x, v2d = gg.y + gg.y;
+                for (int i = 0; i < NS; ++i) {
+                    const float tt = fmaf(om[i], gg.z, th[i]);
+                    float sn, cs_;
+                    __sincosf(tt, &sn, &cs_);
+                    a1r[i] = fmaf(gg.x, cs_, a1r[i]);
+                    a1i[i] = fmaf(gg.x, sn, a1i[i]);
+                    a2r[i] = fmaf(gg.y, cs_, a2r[i]);
+                    a2i[i] = fmaf(gg.y, sn, a2i[i]);
+                }
+                if (NP > 0) {
+                    const float v1d = gg.x + gg.x, v2d = gg.y + gg.y;
 #pragma unroll
-                            for (int i = NS; i < FT; ++i) {
-                                const float hh = fmaf(om[i], gg.z, th[i]);
-                                float cs_, snh;
-                                poly_cis_half(hh, cs_, snh);
-                                a1r[i] = fmaf(gg.x, cs_, a1r[i]);
-                                a1i[i] = fmaf(v1d, snh, a1i[i]);
-                                a2r[i] = fmaf(gg.y, cs_, a2r[i]);
-                                a2i[i] = fmaf(v2d, snh, a2i[i]);
-                            }
-                        }
-                        gg = gn;
+                    for (int i = NS; i < FT; ++i) {
+                        const float hh = fmaf(om[i], gg.z, th[i]);
+                        float cs_, snh;
+                        poly_cis_half(hh, cs_, snh);
+                        a1r[i] = fmaf(gg.x, cs_, a1r[i]);
+                        a1i[i] = fmaf(v1d, snh, a1i[i]);
+                        a2r[i] = fmaf(gg.y, cs_, a2r[i]);
+                        a2i[i] = fmaf(v2d, snh, a2i[i]);
                     }
                 }
-                __syncwarp();
+                gg = gn;
             }
+        }
+        // copy what the window close needs before the buffer is handed back
+        const bool real_particle = warp < S.meta[buf].real;
+        const int64_t out_off = S.meta[buf].out_off;
+        const int glen = S.meta[buf].grid_len, ftile = S.meta[buf].ftile, dir = S.meta[buf].dir;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.gempty[buf]);
 
+        if (flags & kLastOfTile) {
             // ---- window close for this tile: reduce over the block's 8 particles
-            const bool real_particle = (S.item.tile0 + t) * kTileP + warp < S.item.count;
             if (!COH) {
 #pragma unroll
                 for (int i = 0; i < FT; ++i) {
@@ -321,14 +456,14 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                                      a2i[i] * a2i[i];
                     S.red[warp][i][lane] = real_particle ? pw : 0.0f;
                 }
-                named_barrier_sync(1, kComputeWarps * 32);
+                compute_sync(&S.cbar, cphase, lane, abort_flag, p.err_word);
                 for (int v = tid; v < FT * 32; v += kComputeWarps * 32) {
                     double s = 0.0;
 #pragma unroll
                     for (int q = 0; q < kComputeWarps; ++q) s += (double)S.red[q][v >> 5][v & 31];
                     S.run[v] += s;
                 }
-                named_barrier_sync(1, kComputeWarps * 32);
+                compute_sync(&S.cbar, cphase, lane, abort_flag, p.err_word);
             } else {
 #pragma unroll
                 for (int comp = 0; comp < 4; ++comp) {
@@ -338,7 +473,7 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                                         : comp == 2 ? a2r[i] : a2i[i];
                         S.red[warp][i][lane] = real_particle ? val : 0.0f;
                     }
-                    named_barrier_sync(1, kComputeWarps * 32);
+                    compute_sync(&S.cbar, cphase, lane, abort_flag, p.err_word);
                     for (int v = tid; v < FT * 32; v += kComputeWarps * 32) {
                         double s = 0.0;
 #pragma unroll
@@ -346,18 +481,16 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                             s += (double)S.red[q][v >> 5][v & 31];
                         S.run[v * 4 + comp] += s;
                     }
-                    named_barrier_sync(1, kComputeWarps * 32);
+                    compute_sync(&S.cbar, cphase, lane, abort_flag, p.err_word);
                 }
             }
         }
-
-        // ---- item done: add the particle sums to the FP64 accumulators
-        {
-            const ItemSmem& I = S.item;
+        if (flags & kLastOfItem) {
+            // ---- item done: add the particle sums to the FP64 accumulators
             for (int v = tid; v < FT * 32; v += kComputeWarps * 32) {
-                const int k = I.ftile * (32 * FT) + (v & 31) + 32 * (v >> 5);
-                if (k < I.grid_len) {
-                    const int64_t o = I.out_off + (int64_t)I.dir * I.grid_len + k;
+                const int k = ftile * (32 * FT) + (v & 31) + 32 * (v >> 5);
+                if (k < glen) {
+                    const int64_t o = out_off + (int64_t)dir * glen + k;
                     if (!COH) {
                         atomicAdd(p.acc + o, S.run[v]);
                     } else {
@@ -374,8 +507,6 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                 }
             }
         }
-        // everyone is done with S.item before thread 0 overwrites it
-        named_barrier_sync(1, kComputeWarps * 32);
     }
 }
 

@@ -56,14 +56,13 @@ struct rad_ctx {
     int64_t ring = 0, nblk = 0;
     float* slab32 = nullptr;
     double* slab64 = nullptr;
-    double* anchors = nullptr;
+    float* anc32 = nullptr;
     double* x_prev = nullptr;
     double* r_prev = nullptr;
     double* u_prev = nullptr;
 
     // tables
     float* d_dirs32 = nullptr;
-    double* d_dirs64n = nullptr;   // [D][3] n (FP32 path phase)
     double* d_dirs64 = nullptr;    // [D][9] n, e1, e2
     float* d_om32 = nullptr;
     float* d_nuhi = nullptr;
@@ -76,6 +75,7 @@ struct rad_ctx {
     double* acc = nullptr;       // [out_len] or [out_len][4]
     double* d_out = nullptr;     // scaled spectrum staging (device)
     int* d_err = nullptr;
+    int* d_counter = nullptr;    // dynamic item counter of the FP32 kernel
 
     // staging for host inputs
     double* stage[2] = {nullptr, nullptr};
@@ -197,7 +197,7 @@ static void build_items(rad_ctx* c, Event& ev, int total_blocks)
             if ((W.species_mask >> s) & 1u)
                 units += (double)((c->species[s].count + kTileP - 1) / kTileP) * nft * c->D;
     }
-    const double target_items = 8.0 * std::max(1, total_blocks);
+    const double target_items = 64.0 * std::max(1, total_blocks);
     int G = (int)std::max(1.0, std::floor(units / target_items));
     ev.items.clear();
     std::vector<int64_t> cost;
@@ -256,7 +256,7 @@ static int freeze(rad_ctx* c)
     if (c->frozen) return RAD_OK;
     CU(cudaSetDevice(c->device));
     if (c->precision == RAD_FP32_SPLIT) {
-        c->K = c->opt.anchor_K ? c->opt.anchor_K : 16;
+        c->K = c->opt.anchor_K ? c->opt.anchor_K : 32;
         c->cfg.K = c->K;
         c->cfg.ft = c->opt.freq_per_lane ? c->opt.freq_per_lane : 8;
         c->cfg.np = c->opt.variant == RAD_VARIANT_MIX ? (c->cfg.ft == 8 ? 2 : 4) : 0;
@@ -266,9 +266,9 @@ static int freeze(rad_ctx* c)
             return fail(c, RAD_EINVAL, "16 frequencies per thread is built for 2 blocks per SM only");
         // anchor positions: one FP64 3-vector per particle per K samples of the ring
         c->nblk = c->ring / c->K;
-        if (!c->anchors) {
-            CU(cudaMalloc(&c->anchors, (size_t)c->nblk * 3 * c->ncols * sizeof(double)));
-            CU(cudaMemset(c->anchors, 0, (size_t)c->nblk * 3 * c->ncols * sizeof(double)));
+        if (!c->anc32) {
+            CU(cudaMalloc(&c->anc32, (size_t)c->nblk * 6 * c->ncols * sizeof(float)));
+            CU(cudaMemset(c->anc32, 0, (size_t)c->nblk * 6 * c->ncols * sizeof(float)));
         }
     }
     // events
@@ -332,21 +332,22 @@ static int launch_event(rad_ctx* c, Event& ev)
         Accum32Params p{};
         p.items = ev.d_items;
         p.n_items = (int32_t)ev.items.size();
+        p.counter = c->d_counter;
         p.wins = c->d_wins;
         p.species = c->d_species;
         p.dirs32 = c->d_dirs32;
-        p.dirs64 = c->d_dirs64n;
         p.omega = c->d_om32;
         p.nu_hi = c->d_nuhi;
         p.nu_lo = c->d_nulo;
         p.slab32 = c->slab32;
-        p.anchors = c->anchors;
-        p.ncols = c->ncols;
+        p.anc32 = c->anc32;
         p.ring = c->ring;
         p.nblk = c->nblk;
-        p.dt = c->dt;
+        p.dt_hi = (float)c->dt;
+        p.dt_lo = (float)(c->dt - (double)p.dt_hi);
         p.acc = c->acc;
         p.err_word = c->d_err;
+        CU(cudaMemsetAsync(c->d_counter, 0, sizeof(int), c->stream));
         e = cudaSuccess;
         if (!accum32_dispatch(&p, c->cfg, grid, c->stream, &e, nullptr))
             return fail(c, RAD_EINVAL, "kernel variant not built");
@@ -370,7 +371,7 @@ static int ingest_device(rad_ctx* c, int64_t step0, int64_t n, const double* x, 
     p.u_prev = c->u_prev;
     p.slab32 = c->slab32;
     p.slab64 = c->slab64;
-    p.anchors = c->anchors;
+    p.anc32 = c->anc32;
     p.ncols = c->ncols;
     p.ring = c->ring;
     p.K = c->K;
@@ -502,8 +503,8 @@ int rad_init(rad_ctx** out, const double* dirs, int32_t D, const double* freqs,
             return bail(e_ == cudaErrorMemoryAllocation ? RAD_ENOMEM : RAD_ECUDA); \
     } while (0)
     // directions and bases
-    std::vector<float> d32((size_t)D * 9);
-    std::vector<double> d64n((size_t)D * 3), d64((size_t)D * 9);
+    std::vector<float> d32((size_t)D * 12);
+    std::vector<double> d64((size_t)D * 9);
     for (int d = 0; d < D; ++d) {
         double n[3] = {dirs[3 * d], dirs[3 * d + 1], dirs[3 * d + 2]};
         double l = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
@@ -512,10 +513,10 @@ int rad_init(rad_ctx** out, const double* dirs, int32_t D, const double* freqs,
         double e1[3], e2[3];
         basis(n, e1, e2);
         for (int i = 0; i < 3; ++i) {
-            d32[9 * d + i] = (float)n[i];
-            d32[9 * d + 3 + i] = (float)e1[i];
-            d32[9 * d + 6 + i] = (float)e2[i];
-            d64n[3 * d + i] = n[i];
+            d32[12 * d + i] = (float)n[i];
+            d32[12 * d + 3 + i] = (float)e1[i];
+            d32[12 * d + 6 + i] = (float)e2[i];
+            d32[12 * d + 9 + i] = (float)(n[i] - (double)(float)n[i]);
             d64[9 * d + i] = n[i];
             d64[9 * d + 3 + i] = e1[i];
             d64[9 * d + 6 + i] = e2[i];
@@ -544,7 +545,6 @@ int rad_init(rad_ctx** out, const double* dirs, int32_t D, const double* freqs,
         sd[s].count = (int32_t)sp[s].count;
     }
     CUB(cudaMalloc(&c->d_dirs32, d32.size() * sizeof(float)));
-    CUB(cudaMalloc(&c->d_dirs64n, d64n.size() * sizeof(double)));
     CUB(cudaMalloc(&c->d_dirs64, d64.size() * sizeof(double)));
     CUB(cudaMalloc(&c->d_om32, nf * sizeof(float)));
     CUB(cudaMalloc(&c->d_nuhi, nf * sizeof(float)));
@@ -553,7 +553,6 @@ int rad_init(rad_ctx** out, const double* dirs, int32_t D, const double* freqs,
     CUB(cudaMalloc(&c->d_wins, n_win * sizeof(WinDev)));
     CUB(cudaMalloc(&c->d_species, n_species * sizeof(SpeciesDev)));
     CUB(cudaMemcpy(c->d_dirs32, d32.data(), d32.size() * sizeof(float), cudaMemcpyHostToDevice));
-    CUB(cudaMemcpy(c->d_dirs64n, d64n.data(), d64n.size() * sizeof(double), cudaMemcpyHostToDevice));
     CUB(cudaMemcpy(c->d_dirs64, d64.data(), d64.size() * sizeof(double), cudaMemcpyHostToDevice));
     CUB(cudaMemcpy(c->d_om32, om32.data(), nf * sizeof(float), cudaMemcpyHostToDevice));
     CUB(cudaMemcpy(c->d_nuhi, nuh.data(), nf * sizeof(float), cudaMemcpyHostToDevice));
@@ -579,6 +578,7 @@ int rad_init(rad_ctx** out, const double* dirs, int32_t D, const double* freqs,
     CUB(cudaMemset(c->acc, 0, std::max<size_t>(1, acc_n) * sizeof(double)));
     CUB(cudaMalloc(&c->d_out, std::max<int64_t>(1, c->out_len) * sizeof(double)));
     CUB(cudaMalloc(&c->d_err, sizeof(int)));
+    CUB(cudaMalloc(&c->d_counter, sizeof(int)));
     CUB(cudaMemset(c->d_err, 0, sizeof(int)));
     CUB(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
     for (int b = 0; b < 2; ++b) {
@@ -776,9 +776,9 @@ void rad_destroy(rad_ctx* c)
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto& ev : c->events) cudaFree(ev.d_items);
-    void* bufs[] = {c->slab32, c->slab64, c->anchors, c->x_prev, c->r_prev, c->u_prev,
-                    c->d_dirs32, c->d_dirs64n, c->d_dirs64, c->d_om32, c->d_nuhi, c->d_nulo,
-                    c->d_om64, c->d_wins, c->d_species, c->acc, c->d_out, c->d_err,
+    void* bufs[] = {c->slab32, c->slab64, c->anc32, c->x_prev, c->r_prev, c->u_prev,
+                    c->d_dirs32, c->d_dirs64, c->d_om32, c->d_nuhi, c->d_nulo,
+                    c->d_om64, c->d_wins, c->d_species, c->acc, c->d_out, c->d_err, c->d_counter,
                     c->stage[0], c->stage[1]};
     for (void* b : bufs)
         if (b) cudaFree(b);

@@ -74,16 +74,20 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestParams p)
             //   beta_+ - beta_- = du/g_+ - u_- (du.(u_+ + u_-)) / (g_+ g_- (g_+ + g_-)),
             // which has no cancellation for the magnetic (du perpendicular to u)
             // and weakly parallel accelerations a frozen-field push produces.
+            // anchor position r_a as an FP32 hi + lo pair; dr is taken relative
+            // to exactly hi + lo, the value the accumulation kernel sees
+            float* an = p.anc32 + (tile * p.nblk + (m / p.K) % p.nblk) * (6 * kTileP) + pp;
             if ((m % p.K) == 0) {
-                const int64_t blk = (m / p.K) % p.nblk;
                 for (int c = 0; c < 3; ++c) {
-                    ra[c] = rp[c];
-                    p.anchors[(blk * 3 + c) * nc + col] = rp[c];
+                    const float hi = (float)rp[c];
+                    const float lo = (float)(rp[c] - (double)hi);
+                    an[c * kTileP] = hi;
+                    an[(3 + c) * kTileP] = lo;
+                    ra[c] = (double)hi + (double)lo;
                 }
                 have_anchor = true;
             } else if (!have_anchor) {
-                const int64_t blk = (m / p.K) % p.nblk;
-                for (int c = 0; c < 3; ++c) ra[c] = p.anchors[(blk * 3 + c) * nc + col];
+                for (int c = 0; c < 3; ++c) ra[c] = (double)an[c * kTileP] + (double)an[(3 + c) * kTileP];
                 have_anchor = true;
             }
             float um[3], uq[3], du[3], ub[3];

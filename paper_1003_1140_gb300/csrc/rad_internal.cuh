@@ -19,7 +19,9 @@ namespace rad {
 //   beta (3) : beta_m
 //   bdot (3) : betadot_m (differenced in FP64 before the rounding)
 //   g (1)    : 1/gamma_m^2 = 1/(1 + ubar^2)
-// anchors[blk][c][col] double: r_a at samples a = K * blk (ring of blocks).
+// anc32[tile][blk][c][p] float, c = 0..5: r_a as hi (3) + lo (3) FP32 pairs at
+//   the anchor samples a = K * blk (ring of ring/K blocks, tile-major like the
+//   samples, so a chunk's anchors are one contiguous block too).
 // FP64 path: slab64[tile][slot][c][p] double with c = r (3, absolute unwrapped),
 // beta (3), bdot (3), g (1).
 constexpr int kComps = 10;
@@ -58,6 +60,28 @@ struct SpeciesDev {
     int32_t col0;        // first column of the species in the ring
     int32_t count;       // particles
 };
+
+// ---------------------------------------------------------------------------
+// float-float (double-single) helpers: error-free transformations of FP32
+// arithmetic (Dekker/Knuth), used where FP64 accuracy is needed without the
+// FP64 pipe
+// ---------------------------------------------------------------------------
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff two_prod(float a, float b)
+{
+    const float p = a * b;
+    return {p, fmaf(a, b, -p)};
+}
+
+__device__ __forceinline__ ff two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z))};
+}
 
 // ---------------------------------------------------------------------------
 // mbarrier / TMA helpers (inline PTX, sm_90+ forms valid on sm_103a)
@@ -129,6 +153,23 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return false;
 }
 
+// Orders this thread's earlier generic-proxy accesses to shared memory before
+// later async-proxy (bulk copy) writes to it.
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Bounded wait used only to drain copies still in flight after an abort: it
+// polls at most ~2^22 times and never raises flags.
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity)
+{
+    for (uint32_t it = 0; it < kMaxPolls; ++it) {
+        if (mbar_try_wait(bar, parity)) return;
+        __nanosleep(256);
+    }
+}
+
 // 1-D bulk copy (TMA) of `bytes` contiguous bytes into shared memory,
 // completion on `bar`.  Both addresses 16-byte aligned, bytes % 16 == 0.
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
@@ -163,7 +204,7 @@ struct IngestParams {
     double* u_prev;         // [3][ncols] u of the previous call
     float* slab32;          // FP32 ring or nullptr
     double* slab64;         // FP64 ring or nullptr
-    double* anchors;        // FP32 path: [nblk][3][ncols] r at anchor samples
+    float* anc32;           // FP32 path: tile-major anchor ring (r_a as hi + lo)
     int64_t ncols;
     int64_t ring;           // samples in the ring
     int32_t K;              // anchor interval (FP32 path)
@@ -178,19 +219,18 @@ struct IngestParams {
 struct Accum32Params {
     const WorkItem* items;
     int32_t n_items;
+    int* counter;             // dynamic item counter (zeroed before the launch)
     const WinDev* wins;
     const SpeciesDev* species;
-    const float* dirs32;      // [D][9]: n, e1, e2
-    const double* dirs64;     // [D][3]: n
+    const float* dirs32;      // [D][12]: n, e1, e2, n - (float)n
     const float* omega;       // [n_freq] rad per unit time
     const float* nu_hi;       // [n_freq] (omega / 2 pi) hi part
     const float* nu_lo;       // [n_freq] lo part
     const float* slab32;      // tile-major FP32 ring
-    const double* anchors;    // [nblk][3][ncols]
-    int64_t ncols;
+    const float* anc32;       // tile-major anchor ring
     int64_t ring;
     int64_t nblk;
-    double dt;
+    float dt_hi, dt_lo;       // dt as a float-float pair
     double* acc;              // incoherent [n_out]; coherent [n_out][4]
     int* err_word;
 };
