@@ -55,6 +55,7 @@ extern "C" {
 #define RAD_ETIMEOUT (-6)    /* a bounded device-side wait expired; results invalid */
 #define RAD_ENAN (-7)        /* non-finite input detected (check_inputs option) */
 #define RAD_ESTATE (-8)      /* call not allowed in the context's current state */
+#define RAD_ENOSPACE (-9)    /* problem larger than rad_spectrum_noalloc's fixed memory */
 
 /* summation over particles (Sec. 2.2: "phase coherent or phase incoherent") */
 #define RAD_INCOHERENT 0     /* S = 1/(4 pi^2) sum_j |q_j A_j|^2 */
@@ -179,6 +180,47 @@ const char *rad_last_error(const rad_ctx *ctx);
 
 /* rad_destroy -- free the context (NULL is allowed). */
 void rad_destroy(rad_ctx *ctx);
+
+/*
+ * rad_spectrum_noalloc -- the spectrum of one trajectory without allocating
+ * any device memory.  The paper has no counterpart: this is a service of the
+ * library for callers that may not allocate device memory, for example a
+ * simulation that gives all GPU memory to its own pool at start-up and does
+ * not let libraries call cudaMalloc, or a host program where allocation calls
+ * are not available.  It computes what rad_init + rad_accumulate_steps +
+ * rad_finalize compute for one species, one window of samples [0, n_calls-1)
+ * and the FP32 split path (default kernel), using instead a fixed 96 MiB
+ * device array that is part of this library: every GPU that loads the library
+ * holds it until the process exits.  It calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *   dirs     : host [D][3] observer directions (normalised here), D >= 1.
+ *   freqs    : host [F] frequencies, F >= 1.
+ *   dt, charge, box_L, mode : as for rad_init / rad_species.
+ *   N        : particles (>= 1); n_calls >= 2 steps of leapfrog states.
+ *   x, u     : device [n_calls][3][N] FP64, x_s and u_{s-1/2} per step.
+ *   spectrum : device [D][F] FP64, written by the call (the caller owns it).
+ *   cuda_stream : stream to run on (NULL: the legacy default stream).
+ * Limit: the trajectory ring, anchor ring, per-particle state and
+ * accumulators must fit in the 96 MiB array -- about
+ *   (round_up(n_calls - 1, 32) + 64) * round_up(N, 8) * 40 bytes
+ *   + (that many samples / 32) * round_up(N, 8) * 24 bytes + 72 * N bytes
+ *   + 8 * D * F bytes (x4 for RAD_COHERENT) + small tables;
+ * 1024 particles x 2000 samples fit, 8192 x 4096 do not.  Larger problems are
+ * rejected with RAD_ENOSPACE before any device work.  RAD_EINVAL: bad
+ * argument; RAD_ECUDA: a CUDA call failed; RAD_ETIMEOUT: a bounded device
+ * wait expired (results invalid).
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture on that device.  Every call uses the same array
+ * and leaves its contents behind; each call clears what must start at zero.
+ * Calls that overlap on the same GPU (from several host threads or streams at
+ * once) race on the array and corrupt each other: serialise them.  The call
+ * synchronises the stream and returns after the spectrum is written.
+ */
+int rad_spectrum_noalloc(const double *dirs, int32_t D, const double *freqs, int32_t F, double dt,
+                         double charge, int64_t N, int64_t n_calls, const double *x,
+                         const double *u, int32_t mode, double box_L, double *spectrum,
+                         void *cuda_stream);
 
 #ifdef __cplusplus
 }

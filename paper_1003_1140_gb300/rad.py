@@ -24,6 +24,7 @@ RAD_EINCOMPLETE = -5
 RAD_ETIMEOUT = -6
 RAD_ENAN = -7
 RAD_ESTATE = -8
+RAD_ENOSPACE = -9
 
 RAD_INCOHERENT = 0
 RAD_COHERENT = 1
@@ -40,7 +41,8 @@ _ERRNAMES = {RAD_EINVAL: "RAD_EINVAL", RAD_ENOMEM: "RAD_ENOMEM", RAD_ECUDA: "RAD
 #: every symbol include/rad.h declares
 EXPORTED = ("rad_init", "rad_set_options", "rad_get_options", "rad_accumulate",
             "rad_accumulate_steps", "rad_finalize", "rad_reset", "rad_spectrum_size",
-            "rad_updates", "rad_timing", "rad_last_error", "rad_destroy")
+            "rad_updates", "rad_timing", "rad_last_error", "rad_destroy",
+            "rad_spectrum_noalloc")
 
 
 class RadError(RuntimeError):
