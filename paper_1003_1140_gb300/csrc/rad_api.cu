@@ -209,9 +209,12 @@ static void build_items(rad_ctx* c, Event& ev, int total_blocks)
         for (int s = 0; s < c->n_species; ++s) {
             if (!((W.species_mask >> s) & 1u) || c->species[s].count == 0) continue;
             const int nt = (int)((c->species[s].count + kTileP - 1) / kTileP);
-            for (int d = 0; d < c->D; ++d)
-                for (int f = 0; f < nft; ++f)
-                    for (int t0 = 0; t0 < nt; t0 += G) {
+            // tile-group-major: the items that read the same particles
+            // (all directions and frequency tiles) are adjacent in the list,
+            // so they run at about the same time and share L2
+            for (int t0 = 0; t0 < nt; t0 += G)
+                for (int d = 0; d < c->D; ++d)
+                    for (int f = 0; f < nft; ++f) {
                         WorkItem it{w, d, f, s, t0, std::min(G, nt - t0)};
                         ev.items.push_back(it);
                         cost.push_back((int64_t)it.ntiles * nch);
@@ -260,6 +263,7 @@ static int freeze(rad_ctx* c)
         c->cfg.K = c->K;
         c->cfg.ft = c->opt.freq_per_lane ? c->opt.freq_per_lane : 8;
         c->cfg.np = c->opt.variant == RAD_VARIANT_MIX ? (c->cfg.ft == 8 ? 2 : 4) : 0;
+        if (c->opt.variant == RAD_VARIANT_MIX && c->opt.reserved[1] > 0) c->cfg.np = c->opt.reserved[1];
         c->cfg.coh = c->mode == RAD_COHERENT;
         c->cfg.mb = c->opt.blocks_per_sm ? c->opt.blocks_per_sm : 2;
         if (c->cfg.ft == 16 && c->cfg.mb != 2)

@@ -41,14 +41,26 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestParams p)
     bool have_anchor = false;
     bool bad = false;
 
+    // the next step's inputs are loaded while this step is being processed
+    double xq[3], uq[3];
+    for (int c = 0; c < 3; ++c) {
+        xq[c] = p.n_steps > 0 ? p.x[c * p.n_in + i] : 0.0;
+        uq[c] = p.n_steps > 0 ? p.u[c * p.n_in + i] : 0.0;
+    }
     for (int t = 0; t < p.n_steps; ++t) {
         const int64_t s = p.step0 + t;
-        const double* xs = p.x + (int64_t)t * 3 * p.n_in;
-        const double* us = p.u + (int64_t)t * 3 * p.n_in;
         double xn[3], un[3], rn[3];
         for (int c = 0; c < 3; ++c) {
-            xn[c] = xs[c * p.n_in + i];
-            un[c] = us[c * p.n_in + i];
+            xn[c] = xq[c];
+            un[c] = uq[c];
+        }
+        if (t + 1 < p.n_steps) {
+            const double* xs = p.x + (int64_t)(t + 1) * 3 * p.n_in;
+            const double* us = p.u + (int64_t)(t + 1) * 3 * p.n_in;
+            for (int c = 0; c < 3; ++c) {
+                xq[c] = xs[c * p.n_in + i];
+                uq[c] = us[c * p.n_in + i];
+            }
         }
         if (p.check) {
             for (int c = 0; c < 3; ++c) bad |= !isfinite(xn[c]) || !isfinite(un[c]);

@@ -191,6 +191,8 @@ class Radiation:
         for k, v in kw.items():
             if k == "time_ingest":
                 o.reserved[0] = int(v)
+            elif k == "poly_per_lane":
+                o.reserved[1] = int(v)
             else:
                 setattr(o, k, int(v))
         self._check(self._lib.rad_set_options(self._h, ctypes.byref(o)))
