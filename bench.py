@@ -35,6 +35,13 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "G particle·step·ω·n updates/s, FP32 split vs FP64 GPU at ≤1e-4 rel L2"
+
+# DRAM bytes (read + write) of one accumulation launch, from the ncu capture summarised
+# in profiles/accum32_workload2_4096p.md (4096 particles, this workload's samples,
+# directions and omegas), valid while the kernel source and its work-list builder are
+# the ones that were captured; traffic scales with the particle count.
+TRAFFIC_CAPTURE = {"sources_sha256": "d9194926040b71c256573d9bd015e14d518134d34c4df864f01251f65a2c95fe",
+                   "bytes_per_launch": 698.96e6, "particles": 4096}
 UNIT = "G updates/s"
 WORKLOAD = 2
 
@@ -48,7 +55,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-particles", type=int, default=2048)
-    ap.add_argument("--cpu-particles", type=int, default=96)
+    ap.add_argument("--cpu-particles", type=int, default=288)
     ap.add_argument("--particles", type=int, default=None,
                     help="scale the workload to this many particles (profiling cases)")
     ap.add_argument("--variant", type=int, default=None)
@@ -121,6 +128,19 @@ def run_reference(args):
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def captured_traffic(n_particles: int):
+    """DRAM bytes per accumulation launch from the ncu capture, or None if the kernel
+    or its work-list builder changed since the capture."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("paper_1003_1140_gb300/csrc/rad_accum32.cuh", "paper_1003_1140_gb300/csrc/rad_api.cu"):
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != TRAFFIC_CAPTURE["sources_sha256"]:
+        return None
+    return TRAFFIC_CAPTURE["bytes_per_launch"] * n_particles / TRAFFIC_CAPTURE["particles"]
 
 
 # ---------------------------------------------------------------------------
@@ -258,6 +278,7 @@ def main():
     rl = roofline.accum32_roofline(upd * args.steps / max(acc_n, 1), acc_ms / max(acc_n, 1),
                                    torch.cuda.get_device_properties(local).multi_processor_count,
                                    sm_mhz, opts_used)
+    rl["traffic"] = captured_traffic(N)
 
     # end to end through the public API with host buffers (pinned), H2D/D2H inside
     e2e = None
