@@ -96,7 +96,9 @@ typedef struct {
     int32_t freq_per_lane; /* 0 (auto), 8 or 16 frequencies per thread         */
     int32_t defer;         /* 1: evaluate every window in one persistent launch at
                               finalize instead of when its last sample arrives */
-    int32_t use_graph;     /* 1: replay each step's work as a CUDA graph        */
+    int32_t use_graph;     /* 1: FP32 path, one step per call, device inputs: replay
+                              each step's launches (ingest; at a closing step also
+                              the accumulation) as an instantiated CUDA graph    */
     int32_t check_inputs;  /* 1: flag non-finite x/u (RAD_ENAN at finalize)    */
     int32_t blocks_per_sm; /* 0 (auto), 2 or 3: resident blocks per SM the FP32
                               kernel is built for (its register budget)    */

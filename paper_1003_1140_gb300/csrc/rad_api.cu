@@ -9,7 +9,11 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <sstream>
+#include <sys/stat.h>
 #include <map>
 #include <string>
 #include <vector>
@@ -26,11 +30,20 @@ struct Event {
     WorkItem* d_items = nullptr;
 };
 
+// A replayable step: the ingest of one call, followed (for a closing step) by
+// the accumulation of the windows that close there.
+struct StepGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t ingest_node = nullptr;
+};
+
 struct rad_ctx {
     // configuration
     int D = 0;
     int n_grids = 0;
     std::vector<int> grid_off, grid_len;
+    std::vector<double> h_freqs;    // all frequency grids, concatenated
     double dt = 0.0, box_L = 0.0;
     int mode = 0, precision = 0;
     int n_species = 0;
@@ -96,6 +109,11 @@ struct rad_ctx {
     size_t acc_used = 0, ing_used = 0;
     int64_t acc_launches = 0, ing_launches = 0;
     bool time_ingest = false;
+
+    // per-step CUDA graphs (use_graph option), by step kind: index 0 is a
+    // plain step, 1 + e the step that closes event e
+    std::vector<StepGraph> graphs;
+    cudaStream_t cap_stream = nullptr;
 
     std::string err;
 };
@@ -253,6 +271,169 @@ static cudaEvent_t next_event(std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& 
     return pool[used++].second;
 }
 
+// ---------------------------------------------------------------------------
+// autotuner for the FP32 kernel variant (variant = RAD_VARIANT_AUTO)
+// ---------------------------------------------------------------------------
+// Largest anchor interval K whose worst-case phase rounding per update,
+// w_max * |dphi|_max * 2^-24 with |dphi| <= 2 (K - 1) dt, stays within 2e-4 rad.
+static int budget_K(const rad_ctx* c)
+{
+    double wmax = 0.0;
+    for (int g = 0; g < c->n_grids; ++g)
+        for (int k = 0; k < c->grid_len[g]; ++k)
+            wmax = std::max(wmax, std::fabs(c->h_freqs[c->grid_off[g] + k]));
+    for (int K : {32, 16}) {
+        const double err = wmax * 2.0 * (K - 1) * c->dt * std::ldexp(1.0, -24);
+        if (err <= 2e-4) return K;
+    }
+    return 8;
+}
+
+static std::string tune_cache_path()
+{
+    if (const char* e = std::getenv("RAD_AUTOTUNE_CACHE")) return e;
+    if (const char* h = std::getenv("HOME")) return std::string(h) + "/.cache/rad_gb300_autotune.tsv";
+    return "";
+}
+
+static std::string tune_key(const rad_ctx* c, int K)
+{
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, c->device);
+    std::ostringstream k;
+    k << prop.name << "|sm" << c->sms << "|D" << c->D << "|m" << c->mode << "|K" << K << "|g";
+    for (int g = 0; g < c->n_grids; ++g) k << c->grid_len[g] << ",";
+    k << "|s";
+    for (const auto& sp : c->species) k << sp.count << ",";
+    k << "|w";
+    for (const auto& W : c->wins) k << (W.s1 - W.s0) << ":" << W.species_mask << ":" << W.freq_grid << ",";
+    k << "|d" << c->opt.defer;
+    return k.str();
+}
+
+static bool tune_lookup(const std::string& key, Accum32Config& cfg)
+{
+    const std::string path = tune_cache_path();
+    if (path.empty()) return false;
+    std::ifstream f(path);
+    std::string line;
+    bool found = false;
+    while (std::getline(f, line)) {
+        const size_t tab = line.find('\t');
+        if (tab == std::string::npos || line.compare(0, tab, key) != 0 || tab != key.size()) continue;
+        std::istringstream v(line.substr(tab + 1));
+        int ft, np, K, mb;
+        if (v >> ft >> np >> K >> mb) {
+            cfg.ft = ft;
+            cfg.np = np;
+            cfg.K = K;
+            cfg.mb = mb;
+            found = true;   // the last entry for a key wins
+        }
+    }
+    return found;
+}
+
+static void tune_store(const std::string& key, const Accum32Config& cfg)
+{
+    const std::string path = tune_cache_path();
+    if (path.empty()) return;
+    const size_t slash = path.rfind('/');
+    if (slash != std::string::npos && slash > 0) mkdir(path.substr(0, slash).c_str(), 0755);
+    std::ofstream f(path, std::ios::app);
+    if (f) f << key << '\t' << cfg.ft << ' ' << cfg.np << ' ' << cfg.K << ' ' << cfg.mb << '\n';
+}
+
+static int blocks_per_sm(const rad_ctx* c);
+
+// Time the candidate variants on a slice of the real work list (the ring's
+// contents do not change the kernel's instruction stream) and keep the fastest.
+static int autotune32(rad_ctx* c, int K)
+{
+    const std::string key = tune_key(c, K);
+    Accum32Config best = c->cfg;
+    best.K = K;
+    if (tune_lookup(key, best)) {
+        c->cfg = best;
+        c->cfg.coh = c->mode == RAD_COHERENT;
+        return RAD_OK;
+    }
+    const bool coh = c->mode == RAD_COHERENT;
+    std::vector<Accum32Config> cands = {{8, 0, K, coh, 2}, {8, 0, K, coh, 3}, {8, 1, K, coh, 2},
+                                        {8, 2, K, coh, 2}};
+    // small problems: not worth timing
+    if (rad_updates(c) < (int64_t)2e10) {
+        c->cfg = cands[0];
+        return RAD_OK;
+    }
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    for (const auto& cand : cands) {
+        c->cfg = cand;
+        const int bps = blocks_per_sm(c);
+        if (bps < 1) continue;
+        const int total_blocks = bps * c->sms;
+        Event ev;
+        for (size_t w = 0; w < c->wins.size(); ++w)
+            if (c->wins[w].s1 > c->wins[w].s0) ev.wins.push_back((int)w);
+        build_items(c, ev, total_blocks);
+        const size_t n = std::min<size_t>(ev.items.size(), (size_t)4 * total_blocks);
+        if (n == 0) continue;
+        WorkItem* d_items = nullptr;
+        CU(cudaMalloc(&d_items, n * sizeof(WorkItem)));
+        CU(cudaMemcpy(d_items, ev.items.data(), n * sizeof(WorkItem), cudaMemcpyHostToDevice));
+        Accum32Params p{};
+        p.items = d_items;
+        p.n_items = (int32_t)n;
+        p.counter = c->d_counter;
+        p.wins = c->d_wins;
+        p.species = c->d_species;
+        p.dirs32 = c->d_dirs32;
+        p.omega = c->d_om32;
+        p.nu_hi = c->d_nuhi;
+        p.nu_lo = c->d_nulo;
+        p.slab32 = c->slab32;
+        p.anc32 = c->anc32;
+        p.ring = c->ring;
+        p.nblk = c->nblk;
+        p.dt_hi = (float)c->dt;
+        p.dt_lo = (float)(c->dt - (double)p.dt_hi);
+        p.acc = c->acc;
+        p.err_word = c->d_err;
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            CU(cudaMemsetAsync(c->d_counter, 0, sizeof(int), c->stream));
+            CU(cudaEventRecord(e0, c->stream));
+            cudaError_t e = cudaSuccess;
+            accum32_dispatch(&p, cand, (int)std::min<size_t>(n, total_blocks), c->stream, &e, nullptr);
+            CU(e);
+            CU(cudaEventRecord(e1, c->stream));
+            CU(cudaEventSynchronize(e1));
+            float ms = 0;
+            CU(cudaEventElapsedTime(&ms, e0, e1));
+            // per item, so candidates with different item sizes compare fairly
+            ms_min = std::min(ms_min, ms * (float)ev.items.size() / (float)n);
+        }
+        cudaFree(d_items);
+        if (ms_min < best_ms) {
+            best_ms = ms_min;
+            best = cand;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // the timing launches may have added (zero or stale) terms: start clean
+    const size_t acc_n = (size_t)c->out_len * (coh ? 4 : 1);
+    CU(cudaMemsetAsync(c->acc, 0, std::max<size_t>(1, acc_n) * sizeof(double), c->stream));
+    CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    c->cfg = best;
+    tune_store(key, best);
+    return RAD_OK;
+}
+
 // Freeze options: pick K / FT, build events, item lists, TMA map.
 static int freeze(rad_ctx* c)
 {
@@ -268,11 +449,21 @@ static int freeze(rad_ctx* c)
         c->cfg.mb = c->opt.blocks_per_sm ? c->opt.blocks_per_sm : 2;
         if (c->cfg.ft == 16 && c->cfg.mb != 2)
             return fail(c, RAD_EINVAL, "16 frequencies per thread is built for 2 blocks per SM only");
-        // anchor positions: one FP64 3-vector per particle per K samples of the ring
+        const bool tune = c->opt.variant == RAD_VARIANT_AUTO && !c->opt.freq_per_lane &&
+                          !c->opt.blocks_per_sm;
+        if (!c->opt.anchor_K && tune) {
+            c->K = budget_K(c);
+            c->cfg.K = c->K;
+        }
+        // anchor positions: one FP32 hi/lo 3-vector per particle per K samples of the ring
         c->nblk = c->ring / c->K;
         if (!c->anc32) {
             CU(cudaMalloc(&c->anc32, (size_t)c->nblk * 6 * c->ncols * sizeof(float)));
             CU(cudaMemset(c->anc32, 0, (size_t)c->nblk * 6 * c->ncols * sizeof(float)));
+        }
+        if (tune) {
+            const int rc = autotune32(c, c->K);
+            if (rc) return rc;
         }
     }
     // events
@@ -419,6 +610,118 @@ static int ingest_device(rad_ctx* c, int64_t step0, int64_t n, const double* x, 
     return RAD_OK;
 }
 
+// Capture the launches of one step kind on a private stream, instantiate, and
+// remember the ingest kernel node so that each call can patch its inputs in.
+static int graph_for(rad_ctx* c, int kind, const IngestParams& ip, StepGraph** out)
+{
+    if ((int)c->graphs.size() < 1 + (int)c->events.size()) c->graphs.resize(1 + c->events.size());
+    StepGraph& g = c->graphs[kind];
+    if (!g.exec) {
+        if (!c->cap_stream) CU(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        CU(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = launch_ingest(ip, c->cap_stream);
+        if (e == cudaSuccess && kind > 0) {
+            Event& ev = c->events[kind - 1];
+            if (!ev.items.empty()) {
+                const int grid = (int)std::min<int64_t>((int64_t)ev.items.size(), blocks_per_sm(c) * c->sms);
+                Accum32Params p{};
+                p.items = ev.d_items;
+                p.n_items = (int32_t)ev.items.size();
+                p.counter = c->d_counter;
+                p.wins = c->d_wins;
+                p.species = c->d_species;
+                p.dirs32 = c->d_dirs32;
+                p.omega = c->d_om32;
+                p.nu_hi = c->d_nuhi;
+                p.nu_lo = c->d_nulo;
+                p.slab32 = c->slab32;
+                p.anc32 = c->anc32;
+                p.ring = c->ring;
+                p.nblk = c->nblk;
+                p.dt_hi = (float)c->dt;
+                p.dt_lo = (float)(c->dt - (double)p.dt_hi);
+                p.acc = c->acc;
+                p.err_word = c->d_err;
+                e = cudaMemsetAsync(c->d_counter, 0, sizeof(int), c->cap_stream);
+                if (e == cudaSuccess && !accum32_dispatch(&p, c->cfg, grid, c->cap_stream, &e, nullptr))
+                    e = cudaErrorInvalidValue;
+            }
+        }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess)
+            return fail(c, RAD_ECUDA, "step graph capture failed: %s",
+                        cudaGetErrorString(e != cudaSuccess ? e : e2));
+        g.graph = graph;
+        size_t n = 0;
+        CU(cudaGraphGetNodes(graph, nullptr, &n));
+        std::vector<cudaGraphNode_t> nodes(n);
+        CU(cudaGraphGetNodes(graph, nodes.data(), &n));
+        for (auto nd : nodes) {
+            cudaGraphNodeType t;
+            CU(cudaGraphNodeGetType(nd, &t));
+            if (t != cudaGraphNodeTypeKernel) continue;
+            cudaKernelNodeParams kp;
+            CU(cudaGraphKernelNodeGetParams(nd, &kp));
+            if (kp.func == ingest_kernel_ptr()) g.ingest_node = nd;
+        }
+        if (!g.ingest_node) return fail(c, RAD_ECUDA, "ingest node not found in the step graph");
+        CU(cudaGraphInstantiate(&g.exec, graph, 0));
+    }
+    *out = &g;
+    return RAD_OK;
+}
+
+// One step through its graph: patch the ingest node's parameters, replay.
+static int step_via_graph(rad_ctx* c, int64_t step, const double* x, const double* u)
+{
+    IngestParams p{};
+    p.x = x;
+    p.u = u;
+    p.n_in = c->n_in;
+    p.n_steps = 1;
+    p.step0 = step;
+    p.dt = c->dt;
+    p.box_L = c->box_L;
+    p.x_prev = c->x_prev;
+    p.r_prev = c->r_prev;
+    p.u_prev = c->u_prev;
+    p.slab32 = c->slab32;
+    p.slab64 = c->slab64;
+    p.anc32 = c->anc32;
+    p.ncols = c->ncols;
+    p.ring = c->ring;
+    p.K = c->K;
+    p.nblk = c->nblk;
+    p.n_species = c->n_species;
+    for (int s = 0; s <= c->n_species; ++s) p.in_off[s] = c->in_off[s];
+    for (int s = 0; s < c->n_species; ++s) p.col_off[s] = c->col_off[s];
+    p.check = c->opt.check_inputs;
+    p.err_word = c->d_err;
+    int kind = 0;
+    if (!c->opt.defer) {
+        auto itv = c->event_at.find(step);
+        if (itv != c->event_at.end()) kind = 1 + itv->second;
+    }
+    StepGraph* g = nullptr;
+    int rc = graph_for(c, kind, p, &g);
+    if (rc) return rc;
+    cudaKernelNodeParams kp;
+    CU(cudaGraphKernelNodeGetParams(g->ingest_node, &kp));
+    void* args[1] = {&p};
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    CU(cudaGraphExecKernelNodeSetParams(g->exec, g->ingest_node, &kp));
+    if (kind > 0) CU(cudaEventRecord(next_event(c->acc_ev, c->acc_used, true), c->stream));
+    CU(cudaGraphLaunch(g->exec, c->stream));
+    if (kind > 0) {
+        CU(cudaEventRecord(next_event(c->acc_ev, c->acc_used, false), c->stream));
+        ++c->acc_launches;
+    }
+    ++c->ing_launches;
+    return RAD_OK;
+}
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -460,6 +763,7 @@ int rad_init(rad_ctx** out, const double* dirs, int32_t D, const double* freqs,
     }
     for (int64_t i = 0; i < nf; ++i)
         if (!std::isfinite(freqs[i])) return bail(RAD_EINVAL);
+    c->h_freqs.assign(freqs, freqs + nf);
     c->in_off.push_back(0);
     int64_t col = 0;
     for (int s = 0; s < n_species; ++s) {
@@ -636,7 +940,10 @@ int rad_accumulate_steps(rad_ctx* c, int64_t step0, int64_t n, const double* x, 
     if (rc) return rc;
     CU(cudaSetDevice(c->device));
     const bool dx = is_device_ptr(x), du = is_device_ptr(u);
-    if (dx && du) {
+    if (dx && du && n == 1 && c->opt.use_graph && c->precision == RAD_FP32_SPLIT) {
+        rc = step_via_graph(c, step0, x, u);
+        if (rc) return rc;
+    } else if (dx && du) {
         rc = ingest_device(c, step0, n, x, u);
         if (rc) return rc;
     } else {
@@ -798,6 +1105,11 @@ void rad_destroy(rad_ctx* c)
         if (c->copy_done[b]) cudaEventDestroy(c->copy_done[b]);
         if (c->used_done[b]) cudaEventDestroy(c->used_done[b]);
     }
+    for (auto& g : c->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+    }
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     delete c;
 }

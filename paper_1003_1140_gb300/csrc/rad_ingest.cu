@@ -160,6 +160,8 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestParams p)
     if (bad) atomicOr(p.err_word, kErrNaN);
 }
 
+const void* ingest_kernel_ptr() { return reinterpret_cast<const void*>(&ingest_kernel); }
+
 cudaError_t launch_ingest(const IngestParams& p, cudaStream_t st)
 {
     if (p.n_in == 0 || p.n_steps == 0) return cudaSuccess;

@@ -250,6 +250,7 @@ struct Accum64Params {
 };
 
 cudaError_t launch_ingest(const IngestParams& p, cudaStream_t st);
+const void* ingest_kernel_ptr();
 // FP32 kernel variant: frequencies per thread, of which np by the FMA-pipe
 // polynomial, anchor interval K, coherent sum, minimum resident blocks per SM.
 struct Accum32Config {

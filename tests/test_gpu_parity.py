@@ -214,3 +214,71 @@ def test_workload1_full_fp64_and_fp32():
     f32 = _run(w, X, U, R.RAD_FP32_SPLIT)
     assert relL2(f64[0], ref[0]) <= 1e-10
     assert relL2(f32[0], ref[0]) <= 1e-4
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_workload4_structure(precision):
+    """Workload 4's structure, scaled: electrons + ions (m = 16, q = +1), 192 HEALPix
+    directions, three log grids, five uneven windows over both species -- all evaluated in
+    one deferred persistent launch -- against the oracle."""
+    R = _rad()
+    w = trajgen.config(4, 40 / 524288)            # 40 electrons, 2-3 ions
+    scale = 16                                   # windows / 16: 256, 128, 32, 256, 32 samples
+    wins = [(s0 // scale, s1 // scale, m, g) for (s0, s1, m, g) in w.windows]
+    grids = [g[::8] for g in w.grids]            # 64, 128, 256 omegas
+    nc = max(s1 for _, s1, _, _ in wins) + 1
+    X, U = w.trajectory_numpy(n_calls=nc)
+    sp = [(s[0], s[1], s[2]) for s in w.species]
+    ref = oracle.spectra(X, U, w.dt, w.dirs, grids, wins, [(s[0], s[1]) for s in w.species],
+                         box_L=w.L)
+    with R.Radiation(w.dirs, grids, w.dt, sp, wins, precision=precision, box_L=w.L,
+                     options={"defer": 1}) as r:
+        r.accumulate_steps(0, torch.as_tensor(X, device="cuda"), torch.as_tensor(U, device="cuda"))
+        got = r.finalize()
+        t = r.timing()
+    assert t["accum_launches"] == 1
+    _check(got, ref, 1e-10 if precision == 0 else 1e-4, per_direction=True)
+
+
+@pytest.mark.parametrize("coherent", [False, True])
+def test_step_graphs_match_batched_steps(two_species, coherent):
+    """use_graph: one rad_accumulate per step replayed as CUDA graphs (a plain-step
+    graph and one per closing step) gives the batched result."""
+    R = _rad()
+    w, X, U, ref = two_species
+    a = _run(w, X, U, R.RAD_FP32_SPLIT, coherent, device_inputs=True, steps=True)
+    b = _run(w, X, U, R.RAD_FP32_SPLIT, coherent, options={"use_graph": 1},
+             device_inputs=True, steps=False)
+    for g, e in zip(b, a):
+        np.testing.assert_allclose(g, e, rtol=1e-9, atol=1e-300)
+    _check(b, ref[coherent], 1e-4, per_direction=True)
+
+
+def test_autotuner_times_caches_and_reuses(tmp_path, monkeypatch):
+    """variant AUTO on a problem large enough to tune: the choice is written to the
+    on-disk cache, a second context with the same shape reads it back, and the
+    tuned kernel stays within the FP32 tolerance of the fixed default."""
+    R = _rad()
+    from trajgen import gpu as tg
+    cache = tmp_path / "tune.tsv"
+    monkeypatch.setenv("RAD_AUTOTUNE_CACHE", str(cache))
+    w = trajgen.config(2, 4096 / 65536)
+    X, U = tg.trajectory_gpu(w)
+    sp = [(s[0], s[1], s[2]) for s in w.species]
+
+    def run(opts):
+        with R.Radiation(w.dirs, w.grids, w.dt, sp, w.windows, precision=R.RAD_FP32_SPLIT,
+                         box_L=w.L, options=opts) as r:
+            r.accumulate_steps(0, X, U)
+            return r.finalize()[0], r.options()
+
+    s_fixed, _ = run({"variant": 1, "anchor_K": 32})
+    s_auto, o1 = run(None)
+    lines = cache.read_text().strip().splitlines()
+    assert len(lines) == 1 and "\t" in lines[0]
+    s_auto2, o2 = run(None)
+    assert len(cache.read_text().strip().splitlines()) == 1     # reused, not re-tuned
+    assert o1 == o2
+    for S in (s_auto, s_auto2):
+        err = np.linalg.norm(S - s_fixed, axis=1) / np.linalg.norm(s_fixed, axis=1)
+        assert err.max() <= 1e-4
