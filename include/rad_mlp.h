@@ -1,0 +1,71 @@
+/*
+ * rad_mlp.h -- C ABI of the learned surrogate's network.
+ *
+ * The surrogate (a build-side addition to the paper's method, which always
+ * evaluates the full sum of Sec. 2.2) maps a sparse spectrum computed exactly
+ * by the rad_* library to the dense spectrum: a ReLU multilayer perceptron
+ *     h_0 = x,  z_{l+1} = h_l W_l^T + b_l,  h_{l+1} = ReLU(z_{l+1}),  y = z_L,
+ * trained on the mean squared error with Adam.  Arithmetic: BF16 weights (an
+ * FP32 master copy is what Adam updates), BF16 GEMM operands (activations and
+ * backward gradients rounded to BF16 where they enter a product), FP32
+ * accumulation on the tensor cores, FP32 biases, losses accumulated in FP64.
+ * Rounding points (the CPU oracle takes the same): x -> BF16; h_{l+1} =
+ * BF16(ReLU(z_{l+1})); g_L = 2 (y - t)/(B * out) in FP32, BF16 for products;
+ * dW_l = BF16(g_{l+1})^T h_l; g_l = (BF16(g_{l+1}) W_l) * [z_l > 0] in FP32, BF16
+ * for products; db_l = column sums of the FP32 g_{l+1}.
+ *
+ * Every width must be a positive multiple of 128.  Batches are padded to a
+ * multiple of 128 internally (padded rows carry no gradient).  Pointers may
+ * be host or device memory unless stated.  Returns RAD_MLP_OK or a negative
+ * code; calls are stream ordered on the stream given at init and return after
+ * their results are ready.
+ */
+#ifndef RAD_MLP_H
+#define RAD_MLP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RAD_MLP_OK 0
+#define RAD_MLP_EINVAL (-1)
+#define RAD_MLP_ENOMEM (-2)
+#define RAD_MLP_ECUDA (-3)
+
+typedef struct rad_mlp rad_mlp;
+
+/* widths: [n_layers + 1] layer widths (input first); max_batch >= 1. */
+int rad_mlp_init(rad_mlp **out, const int32_t *widths, int32_t n_layers, int32_t max_batch,
+                 void *cuda_stream);
+
+/* Set layer `layer`'s FP32 weights W [out][in] and bias b [out]; resets Adam. */
+int rad_mlp_set_layer(rad_mlp *m, int32_t layer, const float *W, const float *b);
+
+/* Read a layer's FP32 weights, bias and last gradients (any pointer may be NULL). */
+int rad_mlp_get_layer(rad_mlp *m, int32_t layer, float *W, float *b, float *dW, float *db);
+
+/* y [batch][out] = network(x [batch][in]), FP32 in and out. */
+int rad_mlp_forward(rad_mlp *m, int32_t batch, const float *x, float *y);
+
+/* Forward + MSE against t [batch][out] + backward: stores dW, db of every
+ * layer (read them with rad_mlp_get_layer); *loss (host, may be NULL) gets the MSE. */
+int rad_mlp_gradients(rad_mlp *m, int32_t batch, const float *x, const float *t, double *loss);
+
+/* One Adam step from the stored gradients (bias-corrected; FP32 master weights,
+ * BF16 copy refreshed). */
+int rad_mlp_adam(rad_mlp *m, float lr, float beta1, float beta2, float eps);
+
+/* The tensor-core GEMM on its own: C [M][N] (FP32, device) = op(A) op(B), BF16
+ * device operands; AK != 0: A stored [M][K], else [K][M]; BK != 0: B stored
+ * [N][K], else [K][N].  M, N multiples of 128, K of 32.  Default stream. */
+int rad_mlp_gemm(int32_t AK, int32_t BK, int32_t M, int32_t N, int32_t K, const void *A,
+                 const void *B, float *C);
+
+void rad_mlp_destroy(rad_mlp *m);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RAD_MLP_H */

@@ -9,8 +9,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared_symbols():
-    txt = open(os.path.join(ROOT, "include", "rad.h")).read()
+def declared_symbols(header="rad.h"):
+    txt = open(os.path.join(ROOT, "include", header)).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     return sorted(set(re.findall(r"\b(rad_[a-z_0-9]+)\s*\(", txt)))
 
@@ -24,8 +24,14 @@ def test_library_builds_loads_and_exports_everything():
     from paper_1003_1140_gb300 import build
     path = build.build()
     lib = ctypes.CDLL(path)
-    for name in declared_symbols():
-        assert hasattr(lib, name), name
+    for header in ("rad.h", "rad_mlp.h"):
+        for name in declared_symbols(header):
+            assert hasattr(lib, name), name
+
+
+def test_mlp_header_declares_the_binding_names():
+    from paper_1003_1140_gb300 import mlp
+    assert sorted(mlp.EXPORTED) == declared_symbols("rad_mlp.h")
 
 
 def test_null_context_calls_fail_cleanly():
