@@ -159,6 +159,23 @@ int rad_accumulate_steps(rad_ctx *ctx, int64_t step0, int64_t n_steps, const dou
  */
 int rad_finalize(rad_ctx *ctx, double *spectrum);
 
+/*
+ * rad_partial_sums -- the unscaled FP64 particle sums behind the spectrum, for
+ * combining the spectra of particle shards computed in different processes or
+ * on different GPUs (Sec. 2.2: incoherent spectra of disjoint particle sets add;
+ * coherent amplitudes add before the modulus is taken).  out holds, window
+ * after window in rad_finalize's order:
+ *   RAD_INCOHERENT: [n_bins] sum_j |A_j|^2;
+ *   RAD_COHERENT:   [n_bins][4] Re, Im of sum_j A_j . e1 and of sum_j A_j . e2,
+ *   where (e1, e2) is an orthonormal basis of the plane normal to the bin's
+ *   direction that depends only on that direction (so shards with the same
+ *   directions share it).
+ * The spectrum of the union of shards is sum / (4 pi^2) (incoherent) or
+ * (sum of each of the 4 components, squared and added) / (4 pi^2) (coherent).
+ * Same preconditions, synchronisation and errors as rad_finalize.
+ */
+int rad_partial_sums(rad_ctx *ctx, double *out);
+
 /* rad_reset -- forget all steps and zero the accumulators (same configuration). */
 int rad_reset(rad_ctx *ctx);
 

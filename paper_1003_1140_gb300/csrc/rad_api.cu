@@ -725,6 +725,35 @@ static int step_via_graph(rad_ctx* c, int64_t step, const double* x, const doubl
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
+// Everything finalize and the partial-sum export share: every window's last
+// sample must be in, deferred windows are evaluated (once), then `copy` enqueues
+// the output; device-side error flags are checked after the stream drains.
+template <class F>
+static int complete_windows(rad_ctx* c, F copy)
+{
+    if (c->next_step < c->max_s1 + 1)
+        return fail(c, RAD_EINCOMPLETE, "window needs step %lld, last step given is %lld",
+                    (long long)c->max_s1, (long long)c->next_step - 1);
+    int rc = freeze(c);
+    if (rc) return rc;
+    CU(cudaSetDevice(c->device));
+    if (c->opt.defer && !c->deferred_done) {
+        for (auto& ev : c->events) {
+            rc = launch_event(c, ev);
+            if (rc) return rc;
+        }
+        c->deferred_done = true;
+    }
+    rc = copy();
+    if (rc) return rc;
+    int errw = 0;
+    CU(cudaMemcpyAsync(&errw, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (errw & kErrTimeout) return fail(c, RAD_ETIMEOUT, "a device-side wait expired");
+    if (errw & kErrNaN) return fail(c, RAD_ENAN, "non-finite x or u in the input");
+    return RAD_OK;
+}
+
 extern "C" {
 
 int rad_init(rad_ctx** out, const double* dirs, int32_t D, const double* freqs,
@@ -995,33 +1024,32 @@ int rad_finalize(rad_ctx* c, double* spectrum)
 {
     if (!c) return RAD_EINVAL;
     if (!spectrum && c->out_len > 0) return fail(c, RAD_EINVAL, "null spectrum buffer");
-    if (c->next_step < c->max_s1 + 1)
-        return fail(c, RAD_EINCOMPLETE, "window needs step %lld, last step given is %lld",
-                    (long long)c->max_s1, (long long)c->next_step - 1);
-    int rc = freeze(c);
-    if (rc) return rc;
-    CU(cudaSetDevice(c->device));
-    if (c->opt.defer && !c->deferred_done) {
-        for (auto& ev : c->events) {
-            rc = launch_event(c, ev);
-            if (rc) return rc;
+    return complete_windows(c, [&]() -> int {
+        if (c->out_len > 0) {
+            finalize_kernel<<<(unsigned)std::min<int64_t>((c->out_len + 255) / 256, 4096), 256, 0,
+                              c->stream>>>(c->acc, c->d_out, c->out_len, c->mode == RAD_COHERENT);
+            CU(cudaGetLastError());
+            const bool dev = is_device_ptr(spectrum);
+            CU(cudaMemcpyAsync(spectrum, c->d_out, c->out_len * sizeof(double),
+                               dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
         }
-        c->deferred_done = true;
-    }
-    if (c->out_len > 0) {
-        finalize_kernel<<<(unsigned)std::min<int64_t>((c->out_len + 255) / 256, 4096), 256, 0, c->stream>>>(
-            c->acc, c->d_out, c->out_len, c->mode == RAD_COHERENT);
-        CU(cudaGetLastError());
-        const bool dev = is_device_ptr(spectrum);
-        CU(cudaMemcpyAsync(spectrum, c->d_out, c->out_len * sizeof(double),
-                           dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
-    }
-    int errw = 0;
-    CU(cudaMemcpyAsync(&errw, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CU(cudaStreamSynchronize(c->stream));
-    if (errw & kErrTimeout) return fail(c, RAD_ETIMEOUT, "a device-side wait expired");
-    if (errw & kErrNaN) return fail(c, RAD_ENAN, "non-finite x or u in the input");
-    return RAD_OK;
+        return RAD_OK;
+    });
+}
+
+int rad_partial_sums(rad_ctx* c, double* out)
+{
+    if (!c) return RAD_EINVAL;
+    if (!out && c->out_len > 0) return fail(c, RAD_EINVAL, "null output buffer");
+    return complete_windows(c, [&]() -> int {
+        const size_t n = (size_t)c->out_len * (c->mode == RAD_COHERENT ? 4 : 1);
+        if (n > 0) {
+            const bool dev = is_device_ptr(out);
+            CU(cudaMemcpyAsync(out, c->acc, n * sizeof(double),
+                               dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+        }
+        return RAD_OK;
+    });
 }
 
 int rad_reset(rad_ctx* c)

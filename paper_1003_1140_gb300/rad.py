@@ -42,7 +42,7 @@ _ERRNAMES = {RAD_EINVAL: "RAD_EINVAL", RAD_ENOMEM: "RAD_ENOMEM", RAD_ECUDA: "RAD
 EXPORTED = ("rad_init", "rad_set_options", "rad_get_options", "rad_accumulate",
             "rad_accumulate_steps", "rad_finalize", "rad_reset", "rad_spectrum_size",
             "rad_updates", "rad_timing", "rad_last_error", "rad_destroy",
-            "rad_spectrum_noalloc")
+            "rad_spectrum_noalloc", "rad_partial_sums")
 
 
 class RadError(RuntimeError):
@@ -105,6 +105,8 @@ def load(build_if_missing: bool = True):
         lib.rad_accumulate_steps.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, vp, vp]
         lib.rad_finalize.restype = ctypes.c_int
         lib.rad_finalize.argtypes = [vp, vp]
+        lib.rad_partial_sums.restype = ctypes.c_int
+        lib.rad_partial_sums.argtypes = [vp, vp]
         lib.rad_reset.restype = ctypes.c_int
         lib.rad_reset.argtypes = [vp]
         lib.rad_spectrum_size.restype = ctypes.c_int64
@@ -175,6 +177,7 @@ class Radiation:
             self._h = None
             raise RadError(rc, "rad_init failed")
         self.n_windows = len(windows)
+        self.mode = int(mode)
         self.D = dirs.shape[0]
         self.grid_lens = [len(grids[w[3]]) for w in windows]
         if options:
@@ -229,6 +232,15 @@ class Radiation:
             res.append(out[off:off + self.D * L].reshape(self.D, L))
             off += self.D * L
         return res
+
+    def partial_sums(self, out=None):
+        """Unscaled FP64 particle sums (see rad_partial_sums): [n_bins] or [n_bins, 4]."""
+        n = self.spectrum_size() * (4 if self.mode == RAD_COHERENT else 1)
+        host = out is None
+        if host:
+            out = np.empty(n, dtype=np.float64)
+        self._check(self._lib.rad_partial_sums(self._h, _ptr(out)))
+        return out.reshape(-1, 4) if (host and self.mode == RAD_COHERENT) else out
 
     def reset(self):
         self._check(self._lib.rad_reset(self._h))

@@ -282,3 +282,33 @@ def test_autotuner_times_caches_and_reuses(tmp_path, monkeypatch):
     for S in (s_auto, s_auto2):
         err = np.linalg.norm(S - s_fixed, axis=1) / np.linalg.norm(s_fixed, axis=1)
         assert err.max() <= 1e-4
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("coherent", [False, True])
+def test_particle_shards_combine_to_the_whole(two_species, precision, coherent):
+    """Two contexts over disjoint particle halves: their partial sums combine (host
+    reduction) to the spectrum of one context over all particles."""
+    R = _rad()
+    from paper_1003_1140_gb300 import shard
+    w, X, U, ref = two_species
+    Ne = w.species[0][0]
+    halves = [(0, Ne // 2), (Ne // 2, Ne - Ne // 2)]
+    parts = []
+    for first, n in halves:
+        Xs = np.ascontiguousarray(X[:, :, first:first + n])
+        Us = np.ascontiguousarray(U[:, :, first:first + n])
+        win = [(0, 300, 1, 0)]
+        with R.Radiation(w.dirs, w.grids, w.dt, [(n, -1.0, 1.0)], win,
+                         mode=R.RAD_COHERENT if coherent else R.RAD_INCOHERENT,
+                         precision=precision, box_L=w.L) as r:
+            r.accumulate_steps(0, Xs, Us)
+            parts.append(r.partial_sums())
+    S = shard.combine(parts, coherent).reshape(len(w.dirs), -1)
+    Xa, Ua = np.ascontiguousarray(X[:, :, :Ne]), np.ascontiguousarray(U[:, :, :Ne])
+    with R.Radiation(w.dirs, w.grids, w.dt, [(Ne, -1.0, 1.0)], [(0, 300, 1, 0)],
+                     mode=R.RAD_COHERENT if coherent else R.RAD_INCOHERENT,
+                     precision=precision, box_L=w.L) as r:
+        r.accumulate_steps(0, Xa, Ua)
+        whole = r.finalize()[0]
+    np.testing.assert_allclose(S, whole, rtol=1e-9, atol=1e-12 * np.abs(whole).max())

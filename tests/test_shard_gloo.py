@@ -1,0 +1,89 @@
+"""Multi-rank particle sharding (CPU, gloo, world size 2): each rank computes its
+shard's partial sums with the FP64 oracle, the ranks all-reduce them, and the
+spectrum of the union equals the oracle's spectrum of all particles."""
+import math
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _case():
+    import trajgen
+    w = trajgen.config(1, 9 / 1024)
+    X, U = w.trajectory_numpy(n_calls=121)
+    dirs = np.array([[0.0, 1.0, 0.0], [0.6, 0.0, 0.8]])
+    om = np.array([0.3, 3.0, 30.0])
+    return w, X, U, dirs, om
+
+
+def _partial(X, U, w, dirs, om, first, n, coherent):
+    import oracle
+    r, b, bd = oracle.samples(X[:, :, first:first + n], U[:, :, first:first + n], w.dt, w.L)
+    if not coherent:
+        S = oracle.window_spectrum(r, b, bd, -np.ones(n), w.dt, dirs, om, 0, 120)
+        return (S * 4 * math.pi ** 2).reshape(-1)
+    out = np.zeros((len(dirs) * len(om), 6))
+    for d, nv in enumerate(dirs):
+        for j in range(n):
+            A = oracle.amplitude(r, b, bd, j, 0, 120, w.dt, -1.0, nv, om)   # [nf, 3]
+            out[d * len(om):(d + 1) * len(om)] += np.concatenate([A.real, A.imag], 1)
+    return out
+
+
+def _worker(rank, world, port, coherent, result_q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_1003_1140_gb300 import shard
+    w, X, U, dirs, om = _case()
+    first, n = shard.shard(X.shape[2], rank, world)
+    part = _partial(X, U, w, dirs, om, first, n, coherent)
+    S = shard.allreduce_spectrum(part, coherent)
+    if rank == 0:
+        result_q.put(S)
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("coherent", [False, True])
+def test_two_rank_shards_reduce_to_the_full_spectrum(coherent):
+    import multiprocessing as mp
+    import oracle
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, coherent, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    S = q.get(timeout=240)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    w, X, U, dirs, om = _case()
+    ref = oracle.spectra(X, U, w.dt, dirs, [om], [(0, 120, 1, 0)], [(X.shape[2], -1.0)],
+                         coherent=coherent, box_L=w.L)[0].reshape(-1)
+    np.testing.assert_allclose(S, ref, rtol=1e-11)
+
+
+def test_shard_ranges_cover_and_balance():
+    from paper_1003_1140_gb300 import shard
+    for count in (0, 1, 7, 1024, 1025):
+        for world in (1, 2, 3, 8):
+            rs = [shard.shard(count, r, world) for r in range(world)]
+            assert rs[0][0] == 0
+            assert sum(n for _, n in rs) == count
+            for (f0, n0), (f1, _) in zip(rs, rs[1:]):
+                assert f0 + n0 == f1
+            assert max(n for _, n in rs) - min(n for _, n in rs) <= 1
