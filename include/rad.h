@@ -89,6 +89,20 @@ typedef struct {
     int32_t freq_grid;
 } rad_window;
 
+/* Sample selectors (Sec. 2.2: "multiple regions for spectral collection in the
+ * simulation volume"; the momentum pitch-cone selection of Sec. 3.2).  A window
+ * that names a selector only sums the samples inside it (the other samples
+ * contribute nothing, as if the particle did not radiate there). */
+#define RAD_SEL_BOX 1        /* lo <= x_m < hi per component, x_m as handed over */
+#define RAD_SEL_CONE 2       /* |angle(ubar_m, axis) - theta_c| <= dtheta       */
+
+typedef struct {
+    int32_t kind;            /* RAD_SEL_BOX or RAD_SEL_CONE */
+    double lo[3], hi[3];     /* box corners (positions as the PIC hands them over) */
+    double axis[3];          /* cone axis (normalised by the library) */
+    double theta_c, dtheta;  /* cone centre angle and half width, radians */
+} rad_selector;
+
 /* Tuning knobs; zero-initialise for the defaults.  Set before the first step. */
 typedef struct {
     int32_t variant;       /* RAD_VARIANT_*                                  */
@@ -102,7 +116,12 @@ typedef struct {
     int32_t check_inputs;  /* 1: flag non-finite x/u (RAD_ENAN at finalize)    */
     int32_t blocks_per_sm; /* 0 (auto), 2 or 3: resident blocks per SM the FP32
                               kernel is built for (its register budget)    */
-    int32_t reserved[9];
+    int32_t subcycle;      /* 0 or 1: none; n >= 2: n sub-samples per PIC sample
+                              (Sec. 2.2 sub-cycling of the tracked particles):
+                              u linear in time between the half-step states,
+                              betadot its exact derivative, r by Simpson's rule;
+                              updates and the ring grow n-fold               */
+    int32_t reserved[8];
 } rad_options;
 
 /*
@@ -127,6 +146,18 @@ int rad_init(rad_ctx **out, const double *dirs, int32_t D, const double *freqs,
              const int32_t *grid_len, int32_t n_grids, double dt, const rad_species *sp,
              int32_t n_species, const rad_window *win, int32_t n_win, int32_t mode,
              int32_t precision, double box_L, void *cuda_stream);
+
+/*
+ * rad_set_selectors -- define n_sel <= 32 selectors and, for every window,
+ * the selector it uses (window_selector[n_win]: index, or -1 for all samples).
+ * The ingest tests each sample against every selector in FP64: the box on the
+ * position x_m handed over for step m, the cone on
+ * cos(angle) = (ubar_m . axis) / |ubar_m| against [cos(theta_c + dtheta),
+ * cos(theta_c - dtheta)] (angles clamped to [0, pi]).  Call before the first
+ * step (RAD_ESTATE after it); a later call replaces the earlier definition.
+ */
+int rad_set_selectors(rad_ctx *ctx, const rad_selector *sel, int32_t n_sel,
+                      const int32_t *window_selector);
 
 /* rad_set_options -- set tuning knobs; RAD_ESTATE after the first step. */
 int rad_set_options(rad_ctx *ctx, const rad_options *opt);
@@ -221,10 +252,11 @@ void rad_destroy(rad_ctx *ctx);
  *   cuda_stream : stream to run on (NULL: the legacy default stream).
  * Limit: the trajectory ring, anchor ring, per-particle state and
  * accumulators must fit in the 96 MiB array -- about
- *   (round_up(n_calls - 1, 32) + 64) * round_up(N, 8) * 40 bytes
+ *   (round_up(n_calls - 1, 32) + 64) * round_up(N, 8) * 44 bytes
  *   + (that many samples / 32) * round_up(N, 8) * 24 bytes + 72 * N bytes
  *   + 8 * D * F bytes (x4 for RAD_COHERENT) + small tables;
- * 1024 particles x 2000 samples fit, 8192 x 4096 do not.  Larger problems are
+ * (44 bytes with the selector flags), 1024 particles x 2000 samples fit,
+ * 8192 x 4096 do not.  Larger problems are
  * rejected with RAD_ENOSPACE before any device work.  RAD_EINVAL: bad
  * argument; RAD_ECUDA: a CUDA call failed; RAD_ETIMEOUT: a bounded device
  * wait expired (results invalid).

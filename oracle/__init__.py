@@ -114,6 +114,44 @@ def samples(x, u, dt, box_L=0.0):
     return tuple(out)
 
 
+def subsamples(x, u, dt, box_L, nsub):
+    """Sub-cycled samples (Sec. 2.2: tracked particles sub-cycled at a fraction of
+    the PIC step), nsub per PIC sample m, at times (m + tau_k) dt with
+    tau_k = (k + 1/2)/nsub - 1/2:
+      u(tau)       = ubar_m + tau (u_{m+1/2} - u_{m-1/2})       (linear in time)
+      beta(tau)    = u / gamma(u),  gamma = sqrt(1 + u.u)
+      betadot(tau) = udot / gamma - u (u . udot) / gamma^3,  udot = (u_{m+1/2} - u_{m-1/2}) / dt
+      r(tau)       = r_m + dt (tau / 6) (beta(0) + 4 beta(tau/2) + beta(tau))   (Simpson)
+    Returns r, beta, betadot of shape [(n_calls - 1) nsub, 3, N]; sub-sample
+    M = m nsub + k is spaced dt / nsub from its neighbours.
+    """
+    r, _, _ = samples(x, u, dt, box_L)
+    u = np.asarray(u, dtype=np.float64)
+    um, up = u[:-1], u[1:]
+    ubar = 0.5 * (um + up)
+    du = up - um
+
+    def beta_of(uu):
+        return uu / np.sqrt(1.0 + (uu * uu).sum(1, keepdims=True))
+
+    b0 = beta_of(ubar)
+    n_s, _, N = r.shape
+    R = np.empty((n_s, nsub, 3, N))
+    B = np.empty_like(R)
+    BD = np.empty_like(R)
+    for k in range(nsub):
+        tau = (k + 0.5) / nsub - 0.5
+        uk = ubar + tau * du
+        uh = ubar + 0.5 * tau * du
+        gk = np.sqrt(1.0 + (uk * uk).sum(1, keepdims=True))
+        udot = du / dt
+        B[:, k] = uk / gk
+        BD[:, k] = udot / gk - uk * (uk * udot).sum(1, keepdims=True) / gk ** 3
+        R[:, k] = r + dt * (tau / 6.0) * (b0 + 4.0 * beta_of(uh) + uk / gk)
+    shape = (n_s * nsub, 3, N)
+    return R.reshape(shape), B.reshape(shape), BD.reshape(shape)
+
+
 def field(n, beta, betadot):
     """V = n x ((n - beta) x betadot) / (1 - n.beta)^2 for single 3-vectors."""
     n, pn = _c(n)
@@ -165,7 +203,38 @@ def window_spectrum(r, beta, betadot, charge, dt, dirs, omega, s0, s1, coherent=
     return S
 
 
-def spectra(x, u, dt, dirs, grids, windows, species, coherent=False, box_L=0.0):
+def selector_mask(x, u, sel):
+    """Per-sample selection [n_calls - 1, N] (Sec. 2.2 regions for spectral
+    collection; the momentum pitch cone of Sec. 3.2):
+      box : lo <= x_m < hi per component, x_m the position handed over for step m;
+      cone: cos(angle(ubar_m, axis)) in [cos(theta_c + dtheta), cos(theta_c - dtheta)]
+            (angles clamped to [0, pi]), ubar_m = (u_{m-1/2} + u_{m+1/2}) / 2,
+            cos = ((ubar_x a_x + ubar_y a_y) + ubar_z a_z) / sqrt((ubar_x^2 + ubar_y^2) + ubar_z^2).
+    """
+    x = np.asarray(x, dtype=np.float64)
+    u = np.asarray(u, dtype=np.float64)
+    xm = x[:-1]
+    if sel["kind"] == "box":
+        lo = np.asarray(sel["lo"], dtype=np.float64)
+        hi = np.asarray(sel["hi"], dtype=np.float64)
+        ok = np.ones(xm.shape[0:1] + xm.shape[2:], dtype=bool)
+        for q in range(3):
+            ok &= (xm[:, q] >= lo[q]) & (xm[:, q] < hi[q])
+        return ok
+    a = np.asarray(sel["axis"], dtype=np.float64)
+    a = a / np.sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2])
+    ub = 0.5 * (u[:-1] + u[1:])
+    par = (ub[:, 0] * a[0] + ub[:, 1] * a[1]) + ub[:, 2] * a[2]
+    nrm = np.sqrt((ub[:, 0] * ub[:, 0] + ub[:, 1] * ub[:, 1]) + ub[:, 2] * ub[:, 2])
+    with np.errstate(invalid="ignore", divide="ignore"):
+        cs = par / nrm
+    c_lo = np.cos(min(np.pi, sel["theta_c"] + sel["dtheta"]))
+    c_hi = np.cos(max(0.0, sel["theta_c"] - sel["dtheta"]))
+    return (cs >= c_lo) & (cs <= c_hi)
+
+
+def spectra(x, u, dt, dirs, grids, windows, species, coherent=False, box_L=0.0,
+            selectors=None, window_selector=None, subcycle=1):
     """Full diagnostic, in the library's terms, as a list of [D, len(grid)] arrays.
 
     x, u     : [n_calls, 3, N_total] leapfrog states (species concatenated).
@@ -173,8 +242,16 @@ def spectra(x, u, dt, dirs, grids, windows, species, coherent=False, box_L=0.0):
     grids    : list of 1-D frequency arrays.
     windows  : list of (s0, s1, species_mask, grid_index).
     species  : list of (count, charge).
+    selectors, window_selector: optional sample selectors (see selector_mask) and,
+               per window, the selector index or -1; a selected-out sample
+               contributes nothing (its V is zero).
     """
-    r, beta, bdot = samples(x, u, dt, box_L)
+    nsub = max(1, int(subcycle))
+    if nsub == 1:
+        r, beta, bdot = samples(x, u, dt, box_L)
+    else:
+        r, beta, bdot = subsamples(x, u, dt, box_L, nsub)
+    masks = [np.repeat(selector_mask(x, u, sdef), nsub, axis=0) for sdef in (selectors or [])]
     counts = [int(c) for c, _ in species]
     N = int(sum(counts))
     if r.shape[2] != N:
@@ -182,8 +259,11 @@ def spectra(x, u, dt, dirs, grids, windows, species, coherent=False, box_L=0.0):
     sp_index = np.repeat(np.arange(len(species)), counts)
     charge = np.repeat(np.array([float(q) for _, q in species]), counts)
     out = []
-    for (s0, s1, mask, g) in windows:
+    for wi, (s0, s1, mask, g) in enumerate(windows):
         include = ((int(mask) >> sp_index) & 1).astype(np.uint8)
-        out.append(window_spectrum(r, beta, bdot, charge, dt, dirs, grids[g], s0, s1,
-                                   coherent=coherent, include=include))
+        bd = bdot
+        if window_selector is not None and window_selector[wi] >= 0:
+            bd = bdot * masks[window_selector[wi]][:, None, :]   # V is linear in betadot
+        out.append(window_spectrum(r, beta, bd, charge, dt / nsub, dirs, grids[g], s0 * nsub,
+                                   s1 * nsub, coherent=coherent, include=include))
     return out

@@ -224,6 +224,7 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
         float n0 = 0, n1 = 0, n2 = 0, e10 = 0, e11 = 0, e12 = 0, e20 = 0, e21 = 0, e22 = 0;
         float nl0 = 0, nl1 = 0, nl2 = 0, qdt = 0;
         int64_t s0 = 0, s1 = 0, out_off = 0;
+        int selb = -1;
         int grid_len = 0, ftile = 0, dir = 0, count = 0, tile0 = 0;
         uint32_t L = 0;
         for (; cur.valid; ++L) {
@@ -244,6 +245,7 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                 count = p.species[it.sp].count;
                 s0 = w.s0;
                 s1 = w.s1;
+                selb = w.sel;
                 out_off = w.out_off;
                 grid_len = w.grid_len;
                 ftile = it.ftile;
@@ -298,8 +300,9 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                 const float q2 = e20 * d0 + e21 * d1 + e22 * d2;
                 const float kap = bn > 0.0f ? (g + p1 * p1 + p2 * p2) / (1.0f + bn) : 1.0f - bn;
                 const float inv = qdt / (kap * kap);
-                const float V1 = -(p1 * dn + q1 * kap) * inv;
-                const float V2 = -(p2 * dn + q2 * kap) * inv;
+                float V1 = -(p1 * dn + q1 * kap) * inv;
+                float V2 = -(p2 * dn + q2 * kap) * inv;
+                if (selb >= 0 && !((__float_as_uint(tb[10 * kTileP]) >> selb) & 1u)) V1 = V2 = 0.0f;
                 // dphi = ((sm mod K) - (K - 1)) dt - n . dr, compensated
                 const float ti = (float)((sm & (K - 1)) - (K - 1));
                 const ff t = two_prod(ti, p.dt_hi);

@@ -14,7 +14,7 @@ namespace rad {
 
 template <int FT, bool COH>
 struct Smem64 {
-    double tbuf[2][kChunk64][kComps][kTileP];   // 2 x 10240 B
+    double tbuf[2][kChunk64][kComps][kTileP];   // 2 x 11264 B
     double geo[kComputeWarps][kChunk64][4];     // V1, V2, phi, pad
     double red[kComputeWarps][FT][32];
     double run[(COH ? 4 : 1) * FT * 32];
@@ -119,8 +119,10 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
                     const double kap = bn > 0.0 ? (g + p1 * p1 + p2 * p2) / (1.0 + bn) : 1.0 - bn;
                     const double inv = spd.qdt / (kap * kap);
                     const int64_t m = c * kChunk64 + lane;
-                    S.geo[warp][lane][0] = -(p1 * dn + q1 * kap) * inv;
-                    S.geo[warp][lane][1] = -(p2 * dn + q2 * kap) * inv;
+                    const bool keep = w.sel < 0 ||
+                                      ((((uint32_t)tb[10 * kTileP]) >> w.sel) & 1u);
+                    S.geo[warp][lane][0] = keep ? -(p1 * dn + q1 * kap) * inv : 0.0;
+                    S.geo[warp][lane][1] = keep ? -(p2 * dn + q2 * kap) * inv : 0.0;
                     S.geo[warp][lane][2] = (double)m * p.dt - (n0 * r0 + n1 * r1 + n2 * r2);
                 }
                 __syncwarp();

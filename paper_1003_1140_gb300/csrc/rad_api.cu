@@ -57,6 +57,7 @@ struct rad_ctx {
     rad_options opt{};
     Accum32Config cfg{8, 0, 16, false, 2};
     int K = 16;                    // anchor interval used by the ingest
+    int nsub = 1;                  // sub-samples per PIC sample
     bool frozen = false;           // options frozen after the first step
 
     // device / stream
@@ -82,6 +83,9 @@ struct rad_ctx {
     float* d_nulo = nullptr;
     double* d_om64 = nullptr;
     WinDev* d_wins = nullptr;
+    SelectorDev* d_sel = nullptr;
+    int n_sel = 0;
+    std::vector<int32_t> win_sel;
     SpeciesDev* d_species = nullptr;
 
     // accumulators
@@ -223,7 +227,7 @@ static void build_items(rad_ctx* c, Event& ev, int total_blocks)
         const rad_window& W = c->wins[w];
         if (W.s1 <= W.s0) continue;
         const int nft = (c->grid_len[W.freq_grid] + ftl - 1) / ftl;
-        const int64_t nch = (W.s1 - 1) / ch - W.s0 / ch + 1;
+        const int64_t nch = (W.s1 * c->nsub - 1) / ch - W.s0 * c->nsub / ch + 1;
         for (int s = 0; s < c->n_species; ++s) {
             if (!((W.species_mask >> s) & 1u) || c->species[s].count == 0) continue;
             const int nt = (int)((c->species[s].count + kTileP - 1) / kTileP);
@@ -283,7 +287,7 @@ static int budget_K(const rad_ctx* c)
         for (int k = 0; k < c->grid_len[g]; ++k)
             wmax = std::max(wmax, std::fabs(c->h_freqs[c->grid_off[g] + k]));
     for (int K : {32, 16}) {
-        const double err = wmax * 2.0 * (K - 1) * c->dt * std::ldexp(1.0, -24);
+        const double err = wmax * 2.0 * (K - 1) * (c->dt / c->nsub) * std::ldexp(1.0, -24);
         if (err <= 2e-4) return K;
     }
     return 8;
@@ -307,7 +311,7 @@ static std::string tune_key(const rad_ctx* c, int K)
     for (const auto& sp : c->species) k << sp.count << ",";
     k << "|w";
     for (const auto& W : c->wins) k << (W.s1 - W.s0) << ":" << W.species_mask << ":" << W.freq_grid << ",";
-    k << "|d" << c->opt.defer;
+    k << "|d" << c->opt.defer << "|n" << std::max(1, c->opt.subcycle);
     return k.str();
 }
 
@@ -398,8 +402,8 @@ static int autotune32(rad_ctx* c, int K)
         p.anc32 = c->anc32;
         p.ring = c->ring;
         p.nblk = c->nblk;
-        p.dt_hi = (float)c->dt;
-        p.dt_lo = (float)(c->dt - (double)p.dt_hi);
+        p.dt_hi = (float)(c->dt / c->nsub);
+        p.dt_lo = (float)(c->dt / c->nsub - (double)p.dt_hi);
         p.acc = c->acc;
         p.err_word = c->d_err;
         float ms_min = 1e30f;
@@ -439,6 +443,31 @@ static int freeze(rad_ctx* c)
 {
     if (c->frozen) return RAD_OK;
     CU(cudaSetDevice(c->device));
+    if (c->opt.subcycle > 1 && c->nsub == 1) {
+        // sub-cycling: the ring holds nsub samples per PIC sample, windows and
+        // the per-sample weight dt are in sub-sample units
+        c->nsub = c->opt.subcycle;
+        const int64_t nc = c->ncols;
+        const size_t es = c->precision == RAD_FP64 ? sizeof(double) : sizeof(float);
+        void*& slab = c->precision == RAD_FP64 ? reinterpret_cast<void*&>(c->slab64)
+                                               : reinterpret_cast<void*&>(c->slab32);
+        CU(cudaFree(slab));
+        slab = nullptr;
+        c->ring *= c->nsub;
+        CU(cudaMalloc(&slab, (size_t)c->ring * kComps * nc * es));
+        CU(cudaMemset(slab, 0, (size_t)c->ring * kComps * nc * es));
+        std::vector<WinDev> wd(c->wins.size());
+        CU(cudaMemcpy(wd.data(), c->d_wins, wd.size() * sizeof(WinDev), cudaMemcpyDeviceToHost));
+        for (size_t w = 0; w < wd.size(); ++w) {
+            wd[w].s0 = c->wins[w].s0 * c->nsub;
+            wd[w].s1 = c->wins[w].s1 * c->nsub;
+        }
+        CU(cudaMemcpy(c->d_wins, wd.data(), wd.size() * sizeof(WinDev), cudaMemcpyHostToDevice));
+        std::vector<SpeciesDev> sd(c->n_species);
+        CU(cudaMemcpy(sd.data(), c->d_species, sd.size() * sizeof(SpeciesDev), cudaMemcpyDeviceToHost));
+        for (int s = 0; s < c->n_species; ++s) sd[s].qdt = c->species[s].charge * c->dt / c->nsub;
+        CU(cudaMemcpy(c->d_species, sd.data(), sd.size() * sizeof(SpeciesDev), cudaMemcpyHostToDevice));
+    }
     if (c->precision == RAD_FP32_SPLIT) {
         c->K = c->opt.anchor_K ? c->opt.anchor_K : 32;
         c->cfg.K = c->K;
@@ -519,7 +548,7 @@ static int launch_event(rad_ctx* c, Event& ev)
         p.omega = c->d_om64;
         p.slab64 = c->slab64;
         p.ring = c->ring;
-        p.dt = c->dt;
+        p.dt = c->dt / c->nsub;
         p.acc = c->acc;
         p.err_word = c->d_err;
         e = launch_accum64(p, c->mode == RAD_COHERENT, grid, c->stream);
@@ -538,8 +567,8 @@ static int launch_event(rad_ctx* c, Event& ev)
         p.anc32 = c->anc32;
         p.ring = c->ring;
         p.nblk = c->nblk;
-        p.dt_hi = (float)c->dt;
-        p.dt_lo = (float)(c->dt - (double)p.dt_hi);
+        p.dt_hi = (float)(c->dt / c->nsub);
+        p.dt_lo = (float)(c->dt / c->nsub - (double)p.dt_hi);
         p.acc = c->acc;
         p.err_word = c->d_err;
         CU(cudaMemsetAsync(c->d_counter, 0, sizeof(int), c->stream));
@@ -576,6 +605,9 @@ static int ingest_device(rad_ctx* c, int64_t step0, int64_t n, const double* x, 
     for (int s = 0; s < c->n_species; ++s) p.col_off[s] = c->col_off[s];
     p.check = c->opt.check_inputs;
     p.err_word = c->d_err;
+    p.sel = c->d_sel;
+    p.n_sel = c->n_sel;
+    p.nsub = c->nsub;
     int64_t s = step0;
     const int64_t end = step0 + n;
     while (s < end) {
@@ -638,8 +670,8 @@ static int graph_for(rad_ctx* c, int kind, const IngestParams& ip, StepGraph** o
                 p.anc32 = c->anc32;
                 p.ring = c->ring;
                 p.nblk = c->nblk;
-                p.dt_hi = (float)c->dt;
-                p.dt_lo = (float)(c->dt - (double)p.dt_hi);
+                p.dt_hi = (float)(c->dt / c->nsub);
+                p.dt_lo = (float)(c->dt / c->nsub - (double)p.dt_hi);
                 p.acc = c->acc;
                 p.err_word = c->d_err;
                 e = cudaMemsetAsync(c->d_counter, 0, sizeof(int), c->cap_stream);
@@ -698,6 +730,9 @@ static int step_via_graph(rad_ctx* c, int64_t step, const double* x, const doubl
     for (int s = 0; s < c->n_species; ++s) p.col_off[s] = c->col_off[s];
     p.check = c->opt.check_inputs;
     p.err_word = c->d_err;
+    p.sel = c->d_sel;
+    p.n_sel = c->n_sel;
+    p.nsub = c->nsub;
     int kind = 0;
     if (!c->opt.defer) {
         auto itv = c->event_at.find(step);
@@ -874,7 +909,9 @@ int rad_init(rad_ctx** out, const double* dirs, int32_t D, const double* freqs,
         wd[w].grid_off = c->grid_off[win[w].freq_grid];
         wd[w].grid_len = c->grid_len[win[w].freq_grid];
         wd[w].out_off = c->out_off[w];
+        wd[w].sel = -1;
     }
+    c->win_sel.assign(n_win, -1);
     std::vector<SpeciesDev> sd(n_species);
     for (int s = 0; s < n_species; ++s) {
         sd[s].qdt = sp[s].charge * dt;
@@ -888,6 +925,7 @@ int rad_init(rad_ctx** out, const double* dirs, int32_t D, const double* freqs,
     CUB(cudaMalloc(&c->d_nulo, nf * sizeof(float)));
     CUB(cudaMalloc(&c->d_om64, nf * sizeof(double)));
     CUB(cudaMalloc(&c->d_wins, n_win * sizeof(WinDev)));
+    CUB(cudaMalloc(&c->d_sel, kMaxSelectors * sizeof(SelectorDev)));
     CUB(cudaMalloc(&c->d_species, n_species * sizeof(SpeciesDev)));
     CUB(cudaMemcpy(c->d_dirs32, d32.data(), d32.size() * sizeof(float), cudaMemcpyHostToDevice));
     CUB(cudaMemcpy(c->d_dirs64, d64.data(), d64.size() * sizeof(double), cudaMemcpyHostToDevice));
@@ -937,10 +975,61 @@ int rad_set_options(rad_ctx* c, const rad_options* o)
         return fail(c, RAD_EINVAL, "anchor_K must be 0, 8, 16 or 32");
     if (o->freq_per_lane != 0 && o->freq_per_lane != 8 && o->freq_per_lane != 16)
         return fail(c, RAD_EINVAL, "freq_per_lane must be 0, 8 or 16");
+    if (o->subcycle < 0 || o->subcycle > 64)
+        return fail(c, RAD_EINVAL, "subcycle must be in [0, 64]");
     if (o->blocks_per_sm != 0 && o->blocks_per_sm != 2 && o->blocks_per_sm != 3)
         return fail(c, RAD_EINVAL, "blocks_per_sm must be 0, 2 or 3");
     c->opt = *o;
     c->time_ingest = o->reserved[0] != 0;
+    return RAD_OK;
+}
+
+int rad_set_selectors(rad_ctx* c, const rad_selector* sel, int32_t n_sel,
+                      const int32_t* window_selector)
+{
+    if (!c) return RAD_EINVAL;
+    if (c->frozen) return fail(c, RAD_ESTATE, "selectors must be set before the first step");
+    if (n_sel < 0 || n_sel > kMaxSelectors || (n_sel > 0 && !sel) || !window_selector)
+        return fail(c, RAD_EINVAL, "bad selector arguments");
+    std::vector<SelectorDev> h(n_sel);
+    for (int i = 0; i < n_sel; ++i) {
+        const rad_selector& S = sel[i];
+        SelectorDev& d = h[i];
+        d = SelectorDev{};
+        d.kind = S.kind;
+        if (S.kind == RAD_SEL_BOX) {
+            for (int q = 0; q < 3; ++q) {
+                if (!std::isfinite(S.lo[q]) || !std::isfinite(S.hi[q]))
+                    return fail(c, RAD_EINVAL, "selector %d: non-finite box", i);
+                d.lo[q] = S.lo[q];
+                d.hi[q] = S.hi[q];
+            }
+        } else if (S.kind == RAD_SEL_CONE) {
+            const double l = std::sqrt(S.axis[0] * S.axis[0] + S.axis[1] * S.axis[1] +
+                                       S.axis[2] * S.axis[2]);
+            if (!(l > 0.0) || !std::isfinite(l) || !(S.dtheta >= 0.0) || !std::isfinite(S.theta_c))
+                return fail(c, RAD_EINVAL, "selector %d: bad cone", i);
+            for (int q = 0; q < 3; ++q) d.axis[q] = S.axis[q] / l;
+            const double a_hi = std::min(M_PI, S.theta_c + S.dtheta);
+            const double a_lo = std::max(0.0, S.theta_c - S.dtheta);
+            d.cos_lo = std::cos(a_hi);
+            d.cos_hi = std::cos(a_lo);
+        } else {
+            return fail(c, RAD_EINVAL, "selector %d: unknown kind %d", i, S.kind);
+        }
+    }
+    for (size_t w = 0; w < c->wins.size(); ++w)
+        if (window_selector[w] < -1 || window_selector[w] >= n_sel)
+            return fail(c, RAD_EINVAL, "window %zu: selector index out of range", w);
+    CU(cudaSetDevice(c->device));
+    if (n_sel > 0)
+        CU(cudaMemcpy(c->d_sel, h.data(), n_sel * sizeof(SelectorDev), cudaMemcpyHostToDevice));
+    c->n_sel = n_sel;
+    c->win_sel.assign(window_selector, window_selector + c->wins.size());
+    std::vector<WinDev> wd(c->wins.size());
+    CU(cudaMemcpy(wd.data(), c->d_wins, wd.size() * sizeof(WinDev), cudaMemcpyDeviceToHost));
+    for (size_t w = 0; w < wd.size(); ++w) wd[w].sel = c->win_sel[w];
+    CU(cudaMemcpy(c->d_wins, wd.data(), wd.size() * sizeof(WinDev), cudaMemcpyHostToDevice));
     return RAD_OK;
 }
 
@@ -1076,7 +1165,7 @@ int64_t rad_updates(const rad_ctx* c)
             if ((W.species_mask >> s) & 1u) np += c->species[s].count;
         tot += np * (W.s1 - W.s0) * c->D * c->grid_len[W.freq_grid];
     }
-    return tot;
+    return tot * c->nsub;
 }
 
 int rad_timing(rad_ctx* c, double* accum_ms, double* ingest_ms, int64_t* accum_launches,
@@ -1117,7 +1206,7 @@ void rad_destroy(rad_ctx* c)
     for (auto& ev : c->events) cudaFree(ev.d_items);
     void* bufs[] = {c->slab32, c->slab64, c->anc32, c->x_prev, c->r_prev, c->u_prev,
                     c->d_dirs32, c->d_dirs64, c->d_om32, c->d_nuhi, c->d_nulo,
-                    c->d_om64, c->d_wins, c->d_species, c->acc, c->d_out, c->d_err, c->d_counter,
+                    c->d_om64, c->d_wins, c->d_sel, c->d_species, c->acc, c->d_out, c->d_err, c->d_counter,
                     c->stage[0], c->stage[1]};
     for (void* b : bufs)
         if (b) cudaFree(b);

@@ -19,6 +19,31 @@ __device__ __forceinline__ double min_image(double d, double L)
     return L > 0.0 ? d - L * rint(d / L) : d;
 }
 
+// Selector bits of a sample: box tests on the position as handed over, cone
+// tests on cos(angle(ubar, axis)) = ubar.axis / |ubar|, in FP64 without
+// contraction (the oracle takes the same decisions bit for bit).
+__device__ uint32_t selector_bits(const IngestParams& p, const double x[3], const double ub[3])
+{
+    uint32_t bits = 0;
+    for (int i = 0; i < p.n_sel; ++i) {
+        const SelectorDev& S = p.sel[i];
+        bool in = false;
+        if (S.kind == 1) {
+            in = x[0] >= S.lo[0] && x[0] < S.hi[0] && x[1] >= S.lo[1] && x[1] < S.hi[1] &&
+                 x[2] >= S.lo[2] && x[2] < S.hi[2];
+        } else if (S.kind == 2) {
+            const double par = __dadd_rn(__dadd_rn(__dmul_rn(ub[0], S.axis[0]), __dmul_rn(ub[1], S.axis[1])),
+                                         __dmul_rn(ub[2], S.axis[2]));
+            const double nrm = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(ub[0], ub[0]), __dmul_rn(ub[1], ub[1])),
+                                                    __dmul_rn(ub[2], ub[2])));
+            const double cs = __ddiv_rn(par, nrm);
+            in = cs >= S.cos_lo && cs <= S.cos_hi;
+        }
+        bits |= (in ? 1u : 0u) << i;
+    }
+    return bits;
+}
+
 __global__ void __launch_bounds__(256) ingest_kernel(const IngestParams p)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -79,7 +104,78 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestParams p)
         // sample m = s - 1: r_m = rp, u_{m-1/2} = up, u_{m+1/2} = un
         const int64_t m = s - 1;
         const int64_t slot = m % p.ring;
-        if (p.slab32) {
+        if (p.nsub > 1) {
+            // Sub-cycling (Sec. 2.2: tracked particles sub-cycled at
+            // dt_synth <= dt_sim / 10): n sub-samples per PIC sample at
+            // tau = (k + 1/2)/n - 1/2, u(tau) = ubar + tau du linear in time
+            // between the half-step states, betadot the exact derivative of
+            // u/gamma(u) for that u, r(tau) = r_m + dt * Simpson integral of
+            // beta over [0, tau].  Sub-sample M = m n + k lives in ring slot
+            // M mod ring; the samples' selector flags are those of sample m.
+            double ub[3], du[3], b0[3];
+            for (int c = 0; c < 3; ++c) {
+                ub[c] = 0.5 * (up[c] + un[c]);
+                du[c] = un[c] - up[c];
+            }
+            const double g0 = sqrt(1.0 + (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]));
+            for (int c = 0; c < 3; ++c) b0[c] = ub[c] / g0;
+            const uint32_t flags = p.n_sel ? selector_bits(p, xp, ub) : 0xffffffffu;
+            for (int k = 0; k < p.nsub; ++k) {
+                const double tau = (k + 0.5) / p.nsub - 0.5;
+                double uk[3], uh[3], bk[3], bh[3], bd[3], rk[3];
+                for (int c = 0; c < 3; ++c) {
+                    uk[c] = ub[c] + tau * du[c];
+                    uh[c] = ub[c] + 0.5 * tau * du[c];
+                }
+                const double gk2 = 1.0 + (uk[0] * uk[0] + uk[1] * uk[1] + uk[2] * uk[2]);
+                const double gk = sqrt(gk2);
+                const double gh = sqrt(1.0 + (uh[0] * uh[0] + uh[1] * uh[1] + uh[2] * uh[2]));
+                const double udot_u = (uk[0] * du[0] + uk[1] * du[1] + uk[2] * du[2]) / p.dt;
+                for (int c = 0; c < 3; ++c) {
+                    bk[c] = uk[c] / gk;
+                    bh[c] = uh[c] / gh;
+                    bd[c] = (du[c] / p.dt) / gk - uk[c] * udot_u / (gk2 * gk);
+                    rk[c] = rp[c] + p.dt * (tau / 6.0) * (b0[c] + 4.0 * bh[c] + bk[c]);
+                }
+                const int64_t M = m * p.nsub + k;
+                const int64_t sl = M % p.ring;
+                if (p.slab32) {
+                    float* an = p.anc32 + (tile * p.nblk + (M / p.K) % p.nblk) * (6 * kTileP) + pp;
+                    if ((M % p.K) == 0 || !have_anchor) {
+                        if ((M % p.K) == 0) {
+                            for (int c = 0; c < 3; ++c) {
+                                const float hi = (float)rk[c];
+                                const float lo = (float)(rk[c] - (double)hi);
+                                an[c * kTileP] = hi;
+                                an[(3 + c) * kTileP] = lo;
+                                ra[c] = (double)hi + (double)lo;
+                            }
+                        } else {
+                            for (int c = 0; c < 3; ++c)
+                                ra[c] = (double)an[c * kTileP] + (double)an[(3 + c) * kTileP];
+                        }
+                        have_anchor = true;
+                    }
+                    float* o = p.slab32 + (tile * p.ring + sl) * (kComps * kTileP) + pp;
+                    for (int c = 0; c < 3; ++c) {
+                        o[c * kTileP] = (float)(rk[c] - ra[c]);
+                        o[(3 + c) * kTileP] = (float)bk[c];
+                        o[(6 + c) * kTileP] = (float)bd[c];
+                    }
+                    o[9 * kTileP] = (float)(1.0 / gk2);
+                    o[10 * kTileP] = __uint_as_float(flags);
+                } else {
+                    double* o = p.slab64 + (tile * p.ring + sl) * (kComps * kTileP) + pp;
+                    for (int c = 0; c < 3; ++c) {
+                        o[c * kTileP] = rk[c];
+                        o[(3 + c) * kTileP] = bk[c];
+                        o[(6 + c) * kTileP] = bd[c];
+                    }
+                    o[9 * kTileP] = 1.0 / gk2;
+                    o[10 * kTileP] = (double)flags;
+                }
+            }
+        } else if (p.slab32) {
             // FP32 ring: the only cancellation-prone quantities are differenced
             // in FP64 -- du = u_{m+1/2} - u_{m-1/2} and r_m - r_anchor -- and the
             // rest is evaluated in FP32 through the rearrangement
@@ -129,6 +225,12 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestParams p)
             o[7 * kTileP] = (du[1] * igq - um[1] * corr) * idt;
             o[8 * kTileP] = (du[2] * igq - um[2] * corr) * idt;
             o[9 * kTileP] = 1.0f / gb2;
+            {
+                double ubd[3] = {__dmul_rn(0.5, __dadd_rn(up[0], un[0])),
+                                 __dmul_rn(0.5, __dadd_rn(up[1], un[1])),
+                                 __dmul_rn(0.5, __dadd_rn(up[2], un[2]))};
+                o[10 * kTileP] = __uint_as_float(p.n_sel ? selector_bits(p, xp, ubd) : 0xffffffffu);
+            }
         } else {
             double ub[3];
             for (int c = 0; c < 3; ++c) ub[c] = 0.5 * (up[c] + un[c]);
@@ -145,6 +247,12 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestParams p)
                 o[(6 + c) * kTileP] = (un[c] / gp - up[c] / gm) / p.dt;
             }
             o[9 * kTileP] = 1.0 / gb2;
+            {
+                double ubd[3] = {__dmul_rn(0.5, __dadd_rn(up[0], un[0])),
+                                 __dmul_rn(0.5, __dadd_rn(up[1], un[1])),
+                                 __dmul_rn(0.5, __dadd_rn(up[2], un[2]))};
+                o[10 * kTileP] = (double)(p.n_sel ? selector_bits(p, xp, ubd) : 0xffffffffu);
+            }
         }
         for (int c = 0; c < 3; ++c) {
             xp[c] = xn[c];

@@ -19,12 +19,14 @@ namespace rad {
 //   beta (3) : beta_m
 //   bdot (3) : betadot_m (differenced in FP64 before the rounding)
 //   g (1)    : 1/gamma_m^2 = 1/(1 + ubar^2)
+//   flags (1): selector bits of the sample (bit i: inside selector i), stored as
+//              the float with those bits (FP32 ring) or as an exact double (FP64)
 // anc32[tile][blk][c][p] float, c = 0..5: r_a as hi (3) + lo (3) FP32 pairs at
 //   the anchor samples a = K * blk (ring of ring/K blocks, tile-major like the
 //   samples, so a chunk's anchors are one contiguous block too).
 // FP64 path: slab64[tile][slot][c][p] double with c = r (3, absolute unwrapped),
-// beta (3), bdot (3), g (1).
-constexpr int kComps = 10;
+// beta (3), bdot (3), g (1), flags (1).
+constexpr int kComps = 11;   // + selector flags (component 10)
 constexpr int kTileP = 8;      // particles per tile: one warp each
 constexpr int kChunk32 = 32;   // samples per TMA chunk, FP32 ring
 constexpr int kChunk64 = 16;   // samples per TMA chunk, FP64 ring
@@ -53,6 +55,18 @@ struct WinDev {
     int32_t grid_off;    // offset of the frequency grid in the frequency arrays
     int32_t grid_len;    // frequencies in the grid
     int64_t out_off;     // offset of the window's [D][len] block in the accumulators
+    int32_t sel;         // selector bit the samples must have, or -1 (all samples)
+    int32_t pad_;
+};
+
+// A sample selector evaluated at ingest (positions as handed over, ubar).
+constexpr int kMaxSelectors = 32;
+struct SelectorDev {
+    int32_t kind;        // 1: box, 2: cone
+    int32_t pad_;
+    double lo[3], hi[3]; // box: lo <= x < hi per component
+    double axis[3];      // cone: unit axis
+    double cos_lo, cos_hi;  // cone: cos(angle(ubar, axis)) in [cos_lo, cos_hi]
 };
 
 struct SpeciesDev {
@@ -214,6 +228,9 @@ struct IngestParams {
     int32_t col_off[kMaxSpecies];
     int32_t check;          // flag non-finite inputs
     int* err_word;
+    const SelectorDev* sel; // selectors (device) or nullptr
+    int32_t n_sel;
+    int32_t nsub;           // sub-samples per PIC sample (<= 1: none)
 };
 
 struct Accum32Params {

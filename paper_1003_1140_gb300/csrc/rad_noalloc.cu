@@ -170,6 +170,7 @@ extern "C" int rad_spectrum_noalloc(const double* dirs, int32_t D, const double*
     hw->grid_off = 0;
     hw->grid_len = F;
     hw->out_off = 0;
+    hw->sel = -1;
     SpeciesDev* hs = reinterpret_cast<SpeciesDev*>(host.data() + (o_sp - t0));
     hs->qdt = charge * dt;
     hs->col0 = 0;

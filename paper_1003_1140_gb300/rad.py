@@ -42,7 +42,7 @@ _ERRNAMES = {RAD_EINVAL: "RAD_EINVAL", RAD_ENOMEM: "RAD_ENOMEM", RAD_ECUDA: "RAD
 EXPORTED = ("rad_init", "rad_set_options", "rad_get_options", "rad_accumulate",
             "rad_accumulate_steps", "rad_finalize", "rad_reset", "rad_spectrum_size",
             "rad_updates", "rad_timing", "rad_last_error", "rad_destroy",
-            "rad_spectrum_noalloc", "rad_partial_sums")
+            "rad_spectrum_noalloc", "rad_partial_sums", "rad_set_selectors")
 
 
 class RadError(RuntimeError):
@@ -60,11 +60,22 @@ class rad_window(ctypes.Structure):
                 ("freq_grid", ctypes.c_int32)]
 
 
+RAD_SEL_BOX = 1
+RAD_SEL_CONE = 2
+
+
+class rad_selector(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("axis", ctypes.c_double * 3), ("theta_c", ctypes.c_double),
+                ("dtheta", ctypes.c_double)]
+
+
 class rad_options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("anchor_K", ctypes.c_int32),
                 ("freq_per_lane", ctypes.c_int32), ("defer", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("check_inputs", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+                ("blocks_per_sm", ctypes.c_int32), ("subcycle", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 8)]
 
 
 _lock = threading.Lock()
@@ -105,6 +116,9 @@ def load(build_if_missing: bool = True):
         lib.rad_accumulate_steps.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, vp, vp]
         lib.rad_finalize.restype = ctypes.c_int
         lib.rad_finalize.argtypes = [vp, vp]
+        lib.rad_set_selectors.restype = ctypes.c_int
+        lib.rad_set_selectors.argtypes = [vp, ctypes.POINTER(rad_selector), ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_int32)]
         lib.rad_partial_sums.restype = ctypes.c_int
         lib.rad_partial_sums.argtypes = [vp, vp]
         lib.rad_reset.restype = ctypes.c_int
@@ -199,6 +213,26 @@ class Radiation:
             else:
                 setattr(o, k, int(v))
         self._check(self._lib.rad_set_options(self._h, ctypes.byref(o)))
+
+    def set_selectors(self, selectors, window_selector):
+        """selectors: list of dicts {"kind": "box", "lo": [...], "hi": [...]} or
+        {"kind": "cone", "axis": [...], "theta_c": a, "dtheta": d};
+        window_selector: per window, a selector index or -1."""
+        arr = (rad_selector * max(1, len(selectors)))()
+        for i, sdef in enumerate(selectors):
+            r = rad_selector()
+            if sdef["kind"] == "box":
+                r.kind = RAD_SEL_BOX
+                r.lo[:] = [float(v) for v in sdef["lo"]]
+                r.hi[:] = [float(v) for v in sdef["hi"]]
+            else:
+                r.kind = RAD_SEL_CONE
+                r.axis[:] = [float(v) for v in sdef["axis"]]
+                r.theta_c = float(sdef["theta_c"])
+                r.dtheta = float(sdef["dtheta"])
+            arr[i] = r
+        ws = (ctypes.c_int32 * len(window_selector))(*[int(v) for v in window_selector])
+        self._check(self._lib.rad_set_selectors(self._h, arr, len(selectors), ws))
 
     def options(self) -> dict:
         o = rad_options()

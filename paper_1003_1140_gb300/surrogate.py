@@ -224,6 +224,34 @@ def errors(pred, true):
     return lin, rms_dex
 
 
+def gemm_bench(batch=128, reps=20):
+    """Tensor-core throughput of the network's three GEMM shapes at the workload's
+    size (forward X W^T, input gradient G W, weight gradient G^T X of the
+    512 x 393,216 output layer), CUDA-event timed."""
+    import torch
+    from . import mlp as M
+    K, N = 512, 393216
+    res = {}
+    shapes = {"forward": (True, True, batch, N, K), "input_grad": (True, False, batch, K, N),
+              "weight_grad": (False, False, N, K, batch)}
+    for name, (ak, bk, m, n, k) in shapes.items():
+        A = torch.randn((m, k) if ak else (k, m), device="cuda").to(torch.bfloat16)
+        B = torch.randn((n, k) if bk else (k, n), device="cuda").to(torch.bfloat16)
+        C = torch.empty((m, n), dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            M.gemm(A, B, m, n, k, ak, bk, C)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            M.gemm(A, B, m, n, k, ak, bk, C)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"M": m, "N": n, "K": k, "ms": ms, "tflops": 2.0 * m * n * k / (ms * 1e-3) / 1e12}
+    return res
+
+
 def main(argv=None):
     """Train and judge the surrogate; prints one JSON line."""
     import argparse
@@ -236,7 +264,13 @@ def main(argv=None):
     ap.add_argument("--particles", type=int, default=1024)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--gemm-bench", action="store_true")
     a = ap.parse_args(argv)
+    if a.gemm_bench:
+        import json
+        line = json.dumps(gemm_bench())
+        print(line, flush=True)
+        return line
     spec = SurrogateSpec(particles=a.particles)
     t0 = time.perf_counter()
     tr_dense, tr_sparse = generate(spec, range(a.train))

@@ -312,3 +312,49 @@ def test_particle_shards_combine_to_the_whole(two_species, precision, coherent):
         r.accumulate_steps(0, Xa, Ua)
         whole = r.finalize()[0]
     np.testing.assert_allclose(S, whole, rtol=1e-9, atol=1e-12 * np.abs(whole).max())
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("coherent", [False, True])
+def test_selectors_match_oracle(two_species, precision, coherent):
+    """Windows restricted to a spatial box and to a momentum pitch cone about the
+    streaming axis (and one unrestricted window) against the oracle."""
+    R = _rad()
+    w, X, U, _ = two_species
+    sels = [{"kind": "box", "lo": [0, 10, 0], "hi": [40, 30, 25]},
+            {"kind": "cone", "axis": [1, 0, 0], "theta_c": 0.0, "dtheta": 0.2},
+            {"kind": "cone", "axis": [-1, 0, 0], "theta_c": math.pi / 8, "dtheta": 0.3}]
+    wins = [(0, 300, 3, 0), (17, 250, 1, 1), (0, 300, 1, 0), (10, 290, 3, 0)]
+    wsel = [0, 1, 2, -1]
+    sp = [(s[0], s[1], s[2]) for s in w.species]
+    ref = oracle.spectra(X, U, w.dt, w.dirs, w.grids, wins, [(s[0], s[1]) for s in w.species],
+                         coherent=coherent, box_L=w.L, selectors=sels, window_selector=wsel)
+    with R.Radiation(w.dirs, w.grids, w.dt, sp, wins,
+                     mode=R.RAD_COHERENT if coherent else R.RAD_INCOHERENT,
+                     precision=precision, box_L=w.L) as r:
+        r.set_selectors(sels, wsel)
+        r.accumulate_steps(0, torch.as_tensor(X, device="cuda"), torch.as_tensor(U, device="cuda"))
+        got = r.finalize()
+    _check(got, ref, 1e-10 if precision == 0 else 1e-4, per_direction=True)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("coherent", [False, True])
+def test_subcycling_matches_oracle(two_species, precision, coherent):
+    """Sub-cycling (4 sub-samples per PIC sample) with a selector, several windows
+    and both species, against the oracle's sub-cycled sum."""
+    R = _rad()
+    w, X, U, _ = two_species
+    sels = [{"kind": "box", "lo": [0, 10, 0], "hi": [40, 30, 25]}]
+    wsel = [-1, 0, -1, -1]
+    sp = [(s[0], s[1], s[2]) for s in w.species]
+    ref = oracle.spectra(X, U, w.dt, w.dirs, w.grids, w.windows, [(s[0], s[1]) for s in w.species],
+                         coherent=coherent, box_L=w.L, selectors=sels, window_selector=wsel,
+                         subcycle=4)
+    with R.Radiation(w.dirs, w.grids, w.dt, sp, w.windows,
+                     mode=R.RAD_COHERENT if coherent else R.RAD_INCOHERENT,
+                     precision=precision, box_L=w.L, options={"subcycle": 4}) as r:
+        r.set_selectors(sels, wsel)
+        r.accumulate_steps(0, torch.as_tensor(X, device="cuda"), torch.as_tensor(U, device="cuda"))
+        got = r.finalize()
+    _check(got, ref, 1e-10 if precision == 0 else 1e-4, per_direction=True)

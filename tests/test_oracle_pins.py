@@ -430,3 +430,103 @@ def test_fp64_rounding_against_mpmath(small_traj):
             tot += sum(abs(a) ** 2 for a in A)
         ref = float(tot / (4 * mp.pi ** 2))
         assert abs(S[k] - ref) <= 1e-11 * abs(ref) + 1e-300
+
+
+# ---------------------------------------------------------------------------
+# sample selectors (regions / pitch cones)
+# ---------------------------------------------------------------------------
+def test_selector_box_and_cone_hand_cases():
+    # three calls, one particle: x_0 = (1, 1, 1), x_1 = (5, 1, 1); u along x then along y
+    X = np.zeros((3, 3, 1))
+    X[0, :, 0] = [1, 1, 1]
+    X[1, :, 0] = [5, 1, 1]
+    U = np.zeros((3, 3, 1))
+    U[0, 0, 0] = 2.0
+    U[1, 0, 0] = 2.0
+    U[2, 1, 0] = 2.0
+    box = {"kind": "box", "lo": [0, 0, 0], "hi": [4, 4, 4]}
+    assert oracle.selector_mask(X, U, box)[:, 0].tolist() == [True, False]
+    # ubar_0 = (2, 0, 0): angle 0 from x; ubar_1 = (1, 1, 0): 45 degrees
+    cone = {"kind": "cone", "axis": [1, 0, 0], "theta_c": 0.0, "dtheta": 0.1}
+    assert oracle.selector_mask(X, U, cone)[:, 0].tolist() == [True, False]
+    cone45 = {"kind": "cone", "axis": [3, 0, 0], "theta_c": math.pi / 4, "dtheta": 0.01}
+    assert oracle.selector_mask(X, U, cone45)[:, 0].tolist() == [False, True]
+
+
+def test_selector_everything_and_complementary_boxes(small_traj):
+    w, X, U = small_traj
+    N = X.shape[2]
+    dirs = np.array([[0, 1.0, 0], [0.6, 0, 0.8]])
+    om = np.array([0.5, 5.0, 50.0])
+    full = oracle.spectra(X, U, w.dt, dirs, [om], [(0, 150, 1, 0)], [(N, -1.0)], box_L=w.L)[0]
+    every = oracle.spectra(X, U, w.dt, dirs, [om], [(0, 150, 1, 0)], [(N, -1.0)], box_L=w.L,
+                           selectors=[{"kind": "box", "lo": [-1] * 3, "hi": [41] * 3}],
+                           window_selector=[0])[0]
+    np.testing.assert_array_equal(every, full)
+    # complementary halves x < 20, x >= 20: amplitudes (not spectra) add up
+    r, b, bd = oracle.samples(X, U, w.dt, w.L)
+    lo = oracle.selector_mask(X, U, {"kind": "box", "lo": [-1, -1, -1], "hi": [20, 41, 41]})
+    hi = oracle.selector_mask(X, U, {"kind": "box", "lo": [20, -1, -1], "hi": [41, 41, 41]})
+    assert np.all(lo ^ hi)
+    for j in range(N):
+        a = oracle.amplitude(r, b, bd * lo[:, None, :], j, 0, 150, w.dt, -1.0, dirs[1], om)
+        c = oracle.amplitude(r, b, bd * hi[:, None, :], j, 0, 150, w.dt, -1.0, dirs[1], om)
+        t = oracle.amplitude(r, b, bd, j, 0, 150, w.dt, -1.0, dirs[1], om)
+        np.testing.assert_allclose(a + c, t, rtol=1e-12, atol=1e-14 * np.abs(t).max())
+
+
+# ---------------------------------------------------------------------------
+# sub-cycling
+# ---------------------------------------------------------------------------
+def test_subsamples_reduce_to_textbook_cases():
+    # uniform motion: every sub-sample has betadot exactly zero and r on the line
+    u0 = np.array([0.6, -0.2, 0.3])
+    g = math.sqrt(1 + u0 @ u0)
+    nc, dt, n = 6, 0.1, 4
+    U = np.broadcast_to(u0[None, :, None], (nc, 3, 1)).copy()
+    X = (np.arange(nc)[:, None] * dt * u0 / g)[:, :, None]
+    r, b, bd = oracle.subsamples(X, U, dt, 0.0, n)
+    assert np.all(bd == 0.0)
+    t = ((np.arange(nc - 1)[:, None] + ((np.arange(n) + 0.5) / n - 0.5)[None, :]).reshape(-1))
+    np.testing.assert_allclose(r[:, :, 0], t[:, None] * dt * u0 / g, atol=1e-15)
+    # constant force along x from rest-ish: u linear in time, so betadot is the
+    # derivative of u/sqrt(1+u^2) = 1/(1+u^2)^{3/2} * udot
+    U = np.zeros((nc, 3, 1))
+    U[:, 0, 0] = 0.2 + 0.5 * (np.arange(nc) - 0.5) * dt      # u_{s-1/2}
+    X = np.zeros_like(U)
+    r, b, bd = oracle.subsamples(X, U, dt, 0.0, n)
+    ut = 0.2 + 0.5 * t * dt
+    np.testing.assert_allclose(b[:, 0, 0], ut / np.sqrt(1 + ut ** 2), rtol=1e-14)
+    np.testing.assert_allclose(bd[:, 0, 0], 0.5 / (1 + ut ** 2) ** 1.5, rtol=1e-13)
+
+
+def test_subcycling_resolves_what_the_coarse_step_aliases():
+    """A gamma = 3 circle sampled coarsely: sub-cycled spectra approach the spectrum of
+    a 10x finer PIC step at frequencies above the coarse Nyquist frequency."""
+    def circle(dt, nsteps):
+        B0, u = 1.0, math.sqrt(8.0)
+        X = np.zeros((nsteps + 1, 3, 1))
+        U = np.zeros((nsteps + 1, 3, 1))
+        x = np.zeros(3)
+        uu = np.array([u, 0.0, 0.0])
+        for s in range(nsteps + 1):
+            X[s, :, 0] = x
+            U[s, :, 0] = uu
+            g = math.sqrt(1 + uu @ uu)
+            tt = np.array([0, 0, -0.5 * dt * B0 / g])
+            sv = 2 * tt / (1 + tt @ tt)
+            up = uu + np.cross(uu, tt)
+            uu = uu + np.cross(up, sv)
+            x = x + dt * uu / math.sqrt(1 + uu @ uu)
+        return X, U
+    T = 12.0
+    om = np.linspace(8.0, 60.0, 27)      # coarse dt = 0.2: Nyquist ~ pi/0.2 = 16
+    n = np.array([[0.0, 1.0, 0.0]])
+    Xf, Uf = circle(0.02, 600)
+    fine = oracle.spectra(Xf, Uf, 0.02, n, [om], [(0, 600, 1, 0)], [(1, -1.0)])[0][0]
+    Xc, Uc = circle(0.2, 60)
+    coarse = oracle.spectra(Xc, Uc, 0.2, n, [om], [(0, 60, 1, 0)], [(1, -1.0)])[0][0]
+    sub = oracle.spectra(Xc, Uc, 0.2, n, [om], [(0, 60, 1, 0)], [(1, -1.0)], subcycle=10)[0][0]
+    e_coarse = np.linalg.norm(np.log(coarse / fine))
+    e_sub = np.linalg.norm(np.log(sub / fine))
+    assert e_sub < 0.5 * e_coarse, (e_sub, e_coarse)
