@@ -40,8 +40,8 @@ METRIC = "G particle·step·ω·n updates/s, FP32 split vs FP64 GPU at ≤1e-4 r
 # in profiles/accum32_workload2_4096p.md (4096 particles, this workload's samples,
 # directions and omegas), valid while the kernel source and its work-list builder are
 # the ones that were captured; traffic scales with the particle count.
-TRAFFIC_CAPTURE = {"sources_sha256": "d9194926040b71c256573d9bd015e14d518134d34c4df864f01251f65a2c95fe",
-                   "bytes_per_launch": 698.96e6, "particles": 4096}
+TRAFFIC_CAPTURE = {"sources_sha256": "8ba0078ed1d86ae391c2aca0a57103234a3ea3481c0a2e379ac171de74d7d9b0",
+                   "bytes_per_launch": 776.647424e6, "particles": 4096}
 UNIT = "G updates/s"
 WORKLOAD = 2
 
@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--variant", type=int, default=None)
     ap.add_argument("--anchor-K", type=int, default=None)
     ap.add_argument("--freq-per-lane", type=int, default=None)
+    ap.add_argument("--blocks-per-sm", type=int, default=None)
     return ap.parse_args()
 
 
@@ -232,6 +233,8 @@ def main():
         opts["anchor_K"] = args.anchor_K
     if args.freq_per_lane is not None:
         opts["freq_per_lane"] = args.freq_per_lane
+    if args.blocks_per_sm is not None:
+        opts["blocks_per_sm"] = args.blocks_per_sm
     ctx = R.Radiation(w.dirs, w.grids, w.dt, sp, w.windows, precision=R.RAD_FP32_SPLIT,
                       box_L=w.L, options=opts or None)
     out = torch.empty(ctx.spectrum_size(), dtype=torch.float64, device="cuda")

@@ -59,7 +59,10 @@ int rad_mlp_adam(rad_mlp *m, float lr, float beta1, float beta2, float eps);
 
 /* The tensor-core GEMM on its own: C [M][N] (FP32, device) = op(A) op(B), BF16
  * device operands; AK != 0: A stored [M][K], else [K][M]; BK != 0: B stored
- * [N][K], else [K][N].  M, N multiples of 128, K of 32.  Default stream. */
+ * [N][K], else [K][N].  M, N multiples of 128, K of 32.  Default stream.
+ * Products with few 128 x 128 output tiles and a long K are split over K;
+ * their FP32 scratch comes from the default stream's stream-ordered pool
+ * (RAD_MLP_ENOMEM when it cannot be had). */
 int rad_mlp_gemm(int32_t AK, int32_t BK, int32_t M, int32_t N, int32_t K, const void *A,
                  const void *B, float *C);
 

@@ -336,7 +336,14 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                         const float pr = nuh[i] * an.x;
                         const float pe = fmaf(nuh[i], an.x, -pr);
                         const float tl = fmaf(nul[i], an.x, fmaf(nuh[i], an.y, pe));
-                        const float fr = pr - rintf(pr);
+                        // pr minus a nearby integer, on the FP32 pipe (no round
+                        // instruction next to the compute warps' sin/cos): adding
+                        // and removing 1.5 * 2^23 rounds to an integer for
+                        // |pr| < 2^22 and to a float within a few ulp of pr above;
+                        // either difference is exact (Sterbenz), and the second
+                        // pass brings the large-|pr| remainder into [-1/2, 1/2].
+                        float fr = pr - ((pr + kMagic) - kMagic);
+                        fr = fr - ((fr + kMagic) - kMagic);
                         S.ths[buf][pp][b][i][lane] =
                             (fr + tl) * (i < NS ? 6.28318530717958647f : 3.14159265358979323f);
                     }

@@ -8,7 +8,11 @@
 // forward (X W^T), input-gradient (G W) and weight-gradient (G^T X) products
 // all read their operands in place.  Tiles: 128 x 128 x 32 per 256-thread
 // block, cp.async double buffering, epilogue fused (bias, ReLU, ReLU mask of
-// the backward pass, FP32 and/or BF16 output).
+// the backward pass, FP32 and/or BF16 output).  Products with few output
+// tiles and a long K (the input gradient of the wide output layer: 128 x 512
+// outputs over K = 393,216) split K across blocks: each slice writes raw FP32
+// partial sums and one reduction kernel adds the slices in a fixed order and
+// applies the epilogue, so the result does not depend on scheduling.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -26,6 +30,8 @@ typedef __nv_bfloat16 bf16;
 
 constexpr int TM = 128, TN = 128, TK = 32;   // block tile
 constexpr int kGemmThreads = 256;
+constexpr int kSplitTargetBlocks = 2 * 152;  // two resident blocks on each of 152 SMs
+constexpr int kMinSplitTiles = 8;            // K tiles per slice at least
 
 struct Epilogue {
     const float* bias;      // [N] or null
@@ -34,6 +40,17 @@ struct Epilogue {
     bf16* out_bf16;         // [M][N] or null
     int relu;               // apply ReLU before the BF16 store
 };
+
+// Number of K slices for an M x N x K product: enough blocks to fill the GPU
+// twice over when the output alone gives too few, each slice kMinSplitTiles
+// K tiles or more.
+int split_count(int M, int N, int K)
+{
+    const int blocks = (M / TM) * (N / TN), nk = K / TK;
+    if (blocks >= kSplitTargetBlocks / 2) return 1;
+    const int want = (kSplitTargetBlocks + blocks - 1) / blocks;
+    return std::max(1, std::min(want, nk / kMinSplitTiles));
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
@@ -77,7 +94,7 @@ template <bool AK, bool BKC>
 __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_kernel(const bf16* __restrict__ A,
                                                                  const bf16* __restrict__ B, int M,
                                                                  int N, int K, int lda, int ldb,
-                                                                 Epilogue ep)
+                                                                 Epilogue ep, float* partial)
 {
     constexpr int A_ROWS = AK ? TM : TK, A_COLS = (AK ? TK : TM) + 8;
     constexpr int B_ROWS = BKC ? TN : TK, B_COLS = (BKC ? TK : TN) + 8;
@@ -118,13 +135,16 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_kernel(const bf16* __r
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
 
-    const int nk = K / TK;
-    load_stage(0, 0);
+    // K tiles of this block's slice (the whole K range when gridDim.z == 1)
+    const int nk_all = K / TK, S = gridDim.z, z = blockIdx.z;
+    const int kt0 = (int)((int64_t)nk_all * z / S), kt1 = (int)((int64_t)nk_all * (z + 1) / S);
+    const int nk = kt1 - kt0;
+    load_stage(0, kt0 * TK);
     const int r8 = lane & 7, j4 = lane >> 3;
     for (int kt = 0; kt < nk; ++kt) {
         const int st = kt & 1;
         if (kt + 1 < nk) {
-            load_stage(st ^ 1, (kt + 1) * TK);
+            load_stage(st ^ 1, (kt0 + kt + 1) * TK);
             asm volatile("cp.async.wait_group 1;" ::: "memory");
         } else {
             asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -154,6 +174,21 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_kernel(const bf16* __r
         __syncthreads();
     }
 
+    if (partial) {   // split K: raw partial sums of slice z, epilogue in splitk_reduce
+        float* P = partial + (size_t)z * M * N;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int hlf = 0; hlf < 2; ++hlf) {
+                    const int m = m0 + wm * 64 + i * 16 + (lane >> 2) + 8 * hlf;
+                    const int n = n0 + wn * 32 + j * 8 + 2 * (lane & 3);
+                    *reinterpret_cast<float2*>(P + (size_t)m * N + n) =
+                        make_float2(acc[i][j][2 * hlf], acc[i][j][2 * hlf + 1]);
+                }
+        return;
+    }
     // epilogue
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -184,13 +219,57 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_kernel(const bf16* __r
             }
 }
 
+// Sum of the S slices' partials in slice order, then the epilogue of the
+// unsplit kernel (four consecutive outputs per thread; N is a multiple of 128).
+__global__ void splitk_reduce(const float* __restrict__ partial, int S, int M, int N, Epilogue ep)
+{
+    const int64_t MN = (int64_t)M * N, n4 = MN / 4;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = 4 * q;
+        float4 v = *reinterpret_cast<const float4*>(partial + o);
+        for (int s = 1; s < S; ++s) {
+            const float4 p = *reinterpret_cast<const float4*>(partial + s * MN + o);
+            v.x += p.x;
+            v.y += p.y;
+            v.z += p.z;
+            v.w += p.w;
+        }
+        float r[4] = {v.x, v.y, v.z, v.w};
+        const int n = (int)(o % N);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (ep.bias) r[c] += ep.bias[n + c];
+            if (ep.mask) r[c] = ep.mask[o + c] > 0.0f ? r[c] : 0.0f;
+        }
+        if (ep.out_f32) *reinterpret_cast<float4*>(ep.out_f32 + o) = make_float4(r[0], r[1], r[2], r[3]);
+        if (ep.out_bf16) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (ep.relu) r[c] = fmaxf(r[c], 0.0f);
+            __nv_bfloat162* d = reinterpret_cast<__nv_bfloat162*>(ep.out_bf16 + o);
+            d[0] = __floats2bfloat162_rn(r[0], r[1]);
+            d[1] = __floats2bfloat162_rn(r[2], r[3]);
+        }
+    }
+}
+
+// C = op(A) op(B) with the fused epilogue.  work: FP32 scratch of at least
+// split_count(M, N, K) * M * N floats, or null to run unsplit.
 template <bool AK, bool BKC>
 cudaError_t gemm(const bf16* A, const bf16* B, int M, int N, int K, int lda, int ldb,
-                 const Epilogue& ep, cudaStream_t st)
+                 const Epilogue& ep, cudaStream_t st, float* work = nullptr)
 {
     if (M % TM || N % TN || K % TK || lda % 8 || ldb % 8) return cudaErrorInvalidValue;
-    dim3 grid(N / TN, M / TM);
-    gemm_bf16_kernel<AK, BKC><<<grid, kGemmThreads, 0, st>>>(A, B, M, N, K, lda, ldb, ep);
+    const int S = work ? split_count(M, N, K) : 1;
+    dim3 grid(N / TN, M / TM, S);
+    gemm_bf16_kernel<AK, BKC><<<grid, kGemmThreads, 0, st>>>(A, B, M, N, K, lda, ldb, ep,
+                                                             S > 1 ? work : nullptr);
+    if (S > 1) {
+        const int64_t n4 = (int64_t)M * N / 4;
+        const int blocks = (int)std::min<int64_t>((n4 + 255) / 256, 4 * 152);
+        splitk_reduce<<<blocks, 256, 0, st>>>(work, S, M, N, ep);
+    }
     return cudaGetLastError();
 }
 
@@ -293,6 +372,7 @@ struct rad_mlp {
     std::vector<bf16*> gb;          // layer gradients bf16: gb[l] [rows][w[l]] for l >= 1
     double* loss = nullptr;
     float* xin = nullptr;           // staging for host inputs [rows][w[0]]
+    float* work = nullptr;          // split-K partial sums (largest split product)
 };
 
 #define MCU(call)                                            \
@@ -357,6 +437,17 @@ int rad_mlp_init(rad_mlp** out, const int32_t* widths, int32_t n_layers, int32_t
     MAL(m->g, (size_t)R * m->w[n_layers] * 4);
     MAL(m->loss, sizeof(double));
     MAL(m->xin, (size_t)R * m->w[0] * 4);
+    // split-K scratch: the forward and input-gradient products are R rows wide
+    // (the weight gradient reduces over R itself and never splits)
+    size_t work = 0;
+    for (int l = 0; l < n_layers; ++l) {
+        const int in = m->w[l], outw = m->w[l + 1];
+        for (int rows = 128; rows <= R; rows += 128) {
+            work = std::max(work, (size_t)split_count(rows, outw, in) * rows * outw);
+            if (l > 0) work = std::max(work, (size_t)split_count(rows, in, outw) * rows * in);
+        }
+    }
+    MAL(m->work, work * 4);
 #undef MAL
     if (cudaDeviceSynchronize() != cudaSuccess) return bail(RAD_MLP_ECUDA);
     *out = m;
@@ -408,7 +499,8 @@ static int forward(rad_mlp* m, int32_t batch, const float* x)
         const bool last = l == m->L - 1;
         Epilogue ep{m->b[l], nullptr, m->z[l + 1], last ? nullptr : m->h[l + 1], 1};
         // z = h W^T + b: A = h [R][in], B = W [out][in]
-        MCU((gemm<true, true>(m->h[l], m->Wb[l], R, m->w[l + 1], m->w[l], m->w[l], m->w[l], ep, m->st)));
+        MCU((gemm<true, true>(m->h[l], m->Wb[l], R, m->w[l + 1], m->w[l], m->w[l], m->w[l], ep, m->st,
+                              m->work)));
     }
     return RAD_MLP_OK;
 }
@@ -450,7 +542,8 @@ int rad_mlp_gradients(rad_mlp* m, int32_t batch, const float* x, const float* t,
             // G_prev = (G W) * [z_l > 0]: A = G [R][out] (K = out contiguous), B = W [out][in]
             // stored [K][N]; the FP32 product lands in z_l's buffer for the bias sum
             Epilogue eg{nullptr, m->z[l], m->z[l], m->gb[l], 0};
-            MCU((gemm<true, false>(m->gb[l + 1], m->Wb[l], R, in, outw, outw, in, eg, m->st)));
+            MCU((gemm<true, false>(m->gb[l + 1], m->Wb[l], R, in, outw, outw, in, eg, m->st,
+                                   m->work)));
         }
     }
     // bias gradients of the hidden layers: column sums of the FP32 masked products
@@ -485,15 +578,25 @@ int rad_mlp_adam(rad_mlp* m, float lr, float beta1, float beta2, float eps)
 int rad_mlp_gemm(int32_t AK, int32_t BK, int32_t M, int32_t N, int32_t K, const void* A,
                       const void* B, float* C)
 {
+    if (M < 1 || N < 1 || K < 1 || M % TM || N % TN || K % TK || !A || !B || !C)
+        return RAD_MLP_EINVAL;
     Epilogue ep{nullptr, nullptr, C, nullptr, 0};
     const bf16* a = static_cast<const bf16*>(A);
     const bf16* b = static_cast<const bf16*>(B);
+    // split-K scratch from the stream-ordered pool of the default stream
+    float* work = nullptr;
+    const int S = split_count(M, N, K);
+    if (S > 1 && cudaMallocAsync(&work, (size_t)S * M * N * 4, nullptr) != cudaSuccess) {
+        cudaGetLastError();
+        return RAD_MLP_ENOMEM;
+    }
     cudaError_t e;
     const int lda = AK ? K : M, ldb = BK ? K : N;
-    if (AK && BK) e = gemm<true, true>(a, b, M, N, K, lda, ldb, ep, nullptr);
-    else if (AK) e = gemm<true, false>(a, b, M, N, K, lda, ldb, ep, nullptr);
-    else if (BK) e = gemm<false, true>(a, b, M, N, K, lda, ldb, ep, nullptr);
-    else e = gemm<false, false>(a, b, M, N, K, lda, ldb, ep, nullptr);
+    if (AK && BK) e = gemm<true, true>(a, b, M, N, K, lda, ldb, ep, nullptr, work);
+    else if (AK) e = gemm<true, false>(a, b, M, N, K, lda, ldb, ep, nullptr, work);
+    else if (BK) e = gemm<false, true>(a, b, M, N, K, lda, ldb, ep, nullptr, work);
+    else e = gemm<false, false>(a, b, M, N, K, lda, ldb, ep, nullptr, work);
+    if (work) cudaFreeAsync(work, nullptr);
     if (e == cudaErrorInvalidValue) return RAD_MLP_EINVAL;
     return e == cudaSuccess ? RAD_MLP_OK : RAD_MLP_ECUDA;
 }
@@ -508,7 +611,7 @@ void rad_mlp_destroy(rad_mlp* m)
     for (auto* vv : {&m->Wb, &m->h, &m->gb})
         for (bf16* p : *vv)
             if (p) cudaFree(p);
-    for (void* p : {(void*)m->t, (void*)m->g, (void*)m->loss, (void*)m->xin})
+    for (void* p : {(void*)m->t, (void*)m->g, (void*)m->loss, (void*)m->xin, (void*)m->work})
         if (p) cudaFree(p);
     delete m;
 }

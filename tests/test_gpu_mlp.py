@@ -29,6 +29,51 @@ def test_gemm_layouts(ak, bk):
     assert np.abs(got - exp).max() <= 1e-4 * np.abs(exp).max()
 
 
+@pytest.mark.parametrize("ak,bk", [(True, False), (False, True)])
+def test_gemm_split_k(ak, bk):
+    """Two output tiles over K = 32 x 331: the product splits K into 41 slices
+    of 8 or 9 tiles (ragged), reduced in a fixed order."""
+    from paper_1003_1140_gb300 import mlp
+    rng = np.random.default_rng(5)
+    M, N, K = 128, 256, 32 * 331
+    A = ref.bf16(rng.normal(size=(M, K)))
+    B = ref.bf16(rng.normal(size=(N, K)))
+    Ad = _bf16_dev(A if ak else A.T.copy())
+    Bd = _bf16_dev(B if bk else B.T.copy())
+    C = torch.empty((M, N), dtype=torch.float32, device="cuda")
+    mlp.gemm(Ad, Bd, M, N, K, ak, bk, C)
+    C2 = torch.empty_like(C)
+    mlp.gemm(Ad, Bd, M, N, K, ak, bk, C2)
+    exp = A @ B.T
+    got = C.cpu().numpy()
+    # FP32 accumulation of 10,592 products of unit normals: |error| ~ sqrt(K) 2^-24 max|partial|
+    assert np.abs(got - exp).max() <= 1e-4 * np.sqrt(K)
+    assert torch.equal(C, C2)            # the slice order is fixed: bitwise repeatable
+
+
+def test_gradients_split_k_match_reference():
+    """A wide output layer (4096) over a 256-wide hidden layer: the input
+    gradient G W (M = 128, N = 256, K = 4096) runs split over K."""
+    from paper_1003_1140_gb300 import mlp
+    rng = np.random.default_rng(6)
+    widths = [128, 256, 4096]
+    net = mlp.MLP(widths, 100)
+    Ws = [(rng.normal(size=(widths[l + 1], widths[l])) / np.sqrt(widths[l])).astype(np.float32)
+          for l in range(2)]
+    bs = [(rng.normal(size=widths[l + 1]) * 0.1).astype(np.float32) for l in range(2)]
+    for l in range(2):
+        net.set_layer(l, Ws[l], bs[l])
+    x = rng.normal(size=(100, widths[0])).astype(np.float32)
+    t = rng.normal(size=(100, widths[-1])).astype(np.float32)
+    loss = net.gradients(x, t)
+    loss_ref, dW_ref, db_ref = ref.gradients([w.astype(np.float64) for w in Ws], bs, x, t)
+    assert abs(loss - loss_ref) <= 1e-3 * loss_ref
+    for l in range(2):
+        W, b, dW, db = net.get_layer(l, grads=True)
+        assert np.linalg.norm(dW - dW_ref[l]) <= 2e-3 * np.linalg.norm(dW_ref[l]), l
+        assert np.linalg.norm(db - db_ref[l]) <= 2e-3 * np.linalg.norm(db_ref[l]), l
+
+
 def test_gradients_and_adam_match_reference():
     from paper_1003_1140_gb300 import mlp
     rng = np.random.default_rng(3)
