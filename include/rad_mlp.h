@@ -19,6 +19,12 @@
  * be host or device memory unless stated.  Returns RAD_MLP_OK or a negative
  * code; calls are stream ordered on the stream given at init and return after
  * their results are ready.
+ *
+ * The products run on the tcgen05 tensor cores (TMA-staged BF16 tiles, FP32
+ * accumulators in tensor memory).  Every wait inside a GEMM block is bounded;
+ * an expired wait sets a device-wide error word that the next synchronising
+ * call (rad_mlp_forward, rad_mlp_gradients, rad_mlp_check) reports as
+ * RAD_MLP_ETIMEOUT and clears.
  */
 #ifndef RAD_MLP_H
 #define RAD_MLP_H
@@ -33,6 +39,7 @@ extern "C" {
 #define RAD_MLP_EINVAL (-1)
 #define RAD_MLP_ENOMEM (-2)
 #define RAD_MLP_ECUDA (-3)
+#define RAD_MLP_ETIMEOUT (-4) /* a GEMM block's bounded wait expired (results invalid) */
 
 typedef struct rad_mlp rad_mlp;
 
@@ -54,17 +61,26 @@ int rad_mlp_forward(rad_mlp *m, int32_t batch, const float *x, float *y);
 int rad_mlp_gradients(rad_mlp *m, int32_t batch, const float *x, const float *t, double *loss);
 
 /* One Adam step from the stored gradients (bias-corrected; FP32 master weights,
- * BF16 copy refreshed). */
+ * BF16 copies of W and W^T refreshed).  Stream ordered; does not wait. */
 int rad_mlp_adam(rad_mlp *m, float lr, float beta1, float beta2, float eps);
 
 /* The tensor-core GEMM on its own: C [M][N] (FP32, device) = op(A) op(B), BF16
- * device operands; AK != 0: A stored [M][K], else [K][M]; BK != 0: B stored
- * [N][K], else [K][N].  M, N multiples of 128, K of 32.  Default stream.
- * Products with few 128 x 128 output tiles and a long K are split over K;
- * their FP32 scratch comes from the default stream's stream-ordered pool
- * (RAD_MLP_ENOMEM when it cannot be had). */
-int rad_mlp_gemm(int32_t AK, int32_t BK, int32_t M, int32_t N, int32_t K, const void *A,
-                 const void *B, float *C);
+ * device operands (16-byte aligned); a_kcontig != 0: A stored [M][K], else
+ * [K][M]; b_kcontig != 0: B stored [N][K], else [K][N] (operands stored K-last are first
+ * transposed into scratch).  M, N multiples of 128, K of 64.  Default stream;
+ * returns once the work is enqueued.  Products with few 128 x 128 output tiles
+ * and a long K are split over K.  Scratch comes from the default stream's
+ * stream-ordered pool (RAD_MLP_ENOMEM when it cannot be had). */
+int rad_mlp_gemm(int32_t a_kcontig, int32_t b_kcontig, int32_t M, int32_t N, int32_t K,
+                 const void *A, const void *B, float *C);
+
+/* Waits for the device and reports whether any GEMM block's bounded wait
+ * expired since the last check (RAD_MLP_ETIMEOUT), clearing the flag. */
+int rad_mlp_check(void);
+
+/* Text of the last failure of a rad_mlp_* call on the calling host thread
+ * (empty if none; the storage belongs to the library). */
+const char *rad_mlp_last_error(void);
 
 void rad_mlp_destroy(rad_mlp *m);
 

@@ -2,36 +2,96 @@
 // (FP32 master copy), BF16 GEMM operands and FP32 accumulation, trained with
 // MSE and Adam, entirely on the device (C ABI in include/rad_mlp.h).
 //
-// GEMMs run on the tensor cores (mma.sync m16n8k16 BF16 -> FP32) in one kernel
-// template whose operands may be stored K-contiguous or not: ldmatrix (or
-// ldmatrix.trans) reads them from shared memory in the fragment layout, so the
-// forward (X W^T), input-gradient (G W) and weight-gradient (G^T X) products
-// all read their operands in place.  Tiles: 128 x 128 x 32 per 256-thread
-// block, cp.async double buffering, epilogue fused (bias, ReLU, ReLU mask of
-// the backward pass, FP32 and/or BF16 output).  Products with few output
-// tiles and a long K (the input gradient of the wide output layer: 128 x 512
-// outputs over K = 393,216) split K across blocks: each slice writes raw FP32
-// partial sums and one reduction kernel adds the slices in a fixed order and
-// applies the epilogue, so the result does not depend on scheduling.
+// GEMMs run on the 5th-generation tensor cores: one kernel computes
+// C = A B^T for K-contiguous BF16 operands A [M][K], B [N][K].  Per 128 x 128
+// output tile a block of four warps runs a three-stage pipeline:
+//   * warp 0, one lane: TMA (cp.async.bulk.tensor.2d) loads of 128 x 64 tiles
+//     of A and B in the 128-byte-swizzled layout, completion on an mbarrier;
+//   * warp 1, one lane: four tcgen05.mma (kind::f16, BF16 x BF16 -> FP32,
+//     M 128, N 128, K 16) per stage into a 128-column accumulator in tensor
+//     memory; tcgen05.commit frees the stage and, after the last, signals
+//     the epilogue;
+//   * all four warps: tcgen05.ld of their 32 accumulator rows, a transpose
+//     through shared memory into row-contiguous groups, the fused epilogue
+//     (bias, ReLU, ReLU mask of the backward pass, FP32 and/or BF16 output)
+//     and coalesced global stores.
+// Products with few output tiles and a long K (the input gradient of the wide
+// output layer: 128 x 512 outputs over K = 393,216) split K across blocks:
+// each slice writes raw FP32 partial sums and one reduction kernel adds the
+// slices in a fixed order and applies the epilogue, so the result does not
+// depend on scheduling.  The forward product X W^T reads its operands in
+// place; the input gradient G W reads a BF16 copy of W^T (refreshed with W),
+// the weight gradient G^T H reads transposed copies of G and H made per step.
+// Every wait on an mbarrier is bounded; on expiry the block raises an error
+// word, drains what it issued and releases its tensor memory.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <mutex>
 #include <new>
 #include <vector>
 
+#include "rad_internal.cuh"
 #include "rad_mlp.h"
 
 namespace {
 
 typedef __nv_bfloat16 bf16;
+using rad::smem_addr;
 
-constexpr int TM = 128, TN = 128, TK = 32;   // block tile
-constexpr int kGemmThreads = 256;
+constexpr int BM = 128, BN = 128, BK = 64;   // block tile; BK x 2 B = one 128-byte swizzle row
+constexpr int kStages = 3;
+constexpr int kGemmThreads = 128;
+constexpr uint32_t kTileBytes = BM * BK * 2;               // 16 KB per operand per stage
+constexpr uint32_t kStageBytes = 2 * kTileBytes;
+constexpr uint32_t kTmemCols = 128;                        // FP32 accumulator, 128 x 128
+constexpr size_t kGemmSmem = kStages * kStageBytes + 1024 /* alignment */ + 256 /* barriers */;
 constexpr int kSplitTargetBlocks = 2 * 152;  // two resident blocks on each of 152 SMs
-constexpr int kMinSplitTiles = 8;            // K tiles per slice at least
+constexpr int kMinSplitTiles = 4;            // K tiles (of 64) per slice at least
+
+// tcgen05 instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1),
+// A and B BF16 (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0),
+// N / 8 in bits 17-22, M / 16 in bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+// Text of the last failure of a rad_mlp_* call on this host thread.
+thread_local char g_last_error[256] = "";
+
+int fail(int rc, const char* what, cudaError_t e = cudaSuccess)
+{
+    if (e != cudaSuccess)
+        snprintf(g_last_error, sizeof g_last_error, "%s: %s", what, cudaGetErrorString(e));
+    else
+        snprintf(g_last_error, sizeof g_last_error, "%s", what);
+    return rc;
+}
+
+// Raised (bit rad::kErrTimeout) by a GEMM block whose bounded wait expired.
+__device__ int g_gemm_err;
+
+int* gemm_err_word()
+{
+    void* p = nullptr;
+    return cudaGetSymbolAddress(&p, g_gemm_err) == cudaSuccess ? static_cast<int*>(p) : nullptr;
+}
+
+// Reads and clears the error word (after the stream has been synchronised).
+bool gemm_timed_out()
+{
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_gemm_err, sizeof(int)) != cudaSuccess) return true;
+    if (v) {
+        const int zero = 0;
+        cudaMemcpyToSymbol(g_gemm_err, &zero, sizeof(int));
+    }
+    return v != 0;
+}
 
 struct Epilogue {
     const float* bias;      // [N] or null
@@ -46,177 +106,234 @@ struct Epilogue {
 // K tiles or more.
 int split_count(int M, int N, int K)
 {
-    const int blocks = (M / TM) * (N / TN), nk = K / TK;
+    const int blocks = (M / BM) * (N / BN), nk = K / BK;
     if (blocks >= kSplitTargetBlocks / 2) return 1;
     const int want = (kSplitTargetBlocks + blocks - 1) / blocks;
     return std::max(1, std::min(want, nk / kMinSplitTiles));
 }
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p)
+// Shared-memory matrix descriptor of a K-major operand tile stored by TMA with
+// 128-byte swizzling: rows of 128 B, 8-row groups 1024 B apart (stride byte
+// offset), leading byte offset unused for this layout (1), descriptor version
+// 1 (bit 46), layout SWIZZLE_128B (2 in bits 61-63).  The tile base is 1024-B
+// aligned; the k-th 16-element slice starts 32 k bytes further.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
 {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
+           ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_u32(p)));
-}
-
-__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void* p)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_u32(p)));
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
-                                         uint32_t b1)
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar)
 {
     asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
 }
 
-// C[M][N] = op(A) op(B) with op(A) [M][K], op(B)^T [N][K].
-//   AK: A stored [M][K] (row m at A + m lda); else stored [K][M] (row k at A + k lda).
-//   BKC: B stored [N][K] (row n at B + n ldb); else stored [K][N].
-// M, N multiples of 128, K a multiple of 32, leading dimensions multiples of 8.
-template <bool AK, bool BKC>
-__global__ void __launch_bounds__(kGemmThreads) gemm_bf16_kernel(const bf16* __restrict__ A,
-                                                                 const bf16* __restrict__ B, int M,
-                                                                 int N, int K, int lda, int ldb,
-                                                                 Epilogue ep, float* partial)
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t accumulate)
 {
-    constexpr int A_ROWS = AK ? TM : TK, A_COLS = (AK ? TK : TM) + 8;
-    constexpr int B_ROWS = BKC ? TN : TK, B_COLS = (BKC ? TK : TN) + 8;
-    __shared__ __align__(16) bf16 As[2][A_ROWS][A_COLS];
-    __shared__ __align__(16) bf16 Bs[2][B_ROWS][B_COLS];
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp & 1, wn = warp >> 1;           // 2 x 4 warps, 64 x 32 each
-    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+// Arrives on bar once every tcgen05.mma this thread issued before has completed.
+__device__ __forceinline__ void umma_commit(uint64_t* bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_addr(bar))
+        : "memory");
+}
 
-    auto load_stage = [&](int st, int k0) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int c = tid + h * kGemmThreads;     // 512 chunks of 16 B per operand
-            if (AK) {
-                const int r = c >> 2, col = (c & 3) * 8;
-                cp_async16(&As[st][r][col], A + (size_t)(m0 + r) * lda + k0 + col);
-            } else {
-                const int r = c >> 4, col = (c & 15) * 8;
-                cp_async16(&As[st][r][col], A + (size_t)(k0 + r) * lda + m0 + col);
-            }
-            if (BKC) {
-                const int r = c >> 2, col = (c & 3) * 8;
-                cp_async16(&Bs[st][r][col], B + (size_t)(n0 + r) * ldb + k0 + col);
-            } else {
-                const int r = c >> 4, col = (c & 15) * 8;
-                cp_async16(&Bs[st][r][col], B + (size_t)(k0 + r) * ldb + n0 + col);
-            }
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-    float acc[4][4][4];
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
 
-    // K tiles of this block's slice (the whole K range when gridDim.z == 1)
-    const int nk_all = K / TK, S = gridDim.z, z = blockIdx.z;
+// C = A B^T over K tiles [kt0, kt1) of slice blockIdx.z; A, B through the
+// tensor maps (K innermost, box 64 x 128, 128-byte swizzle).
+__global__ void __launch_bounds__(kGemmThreads, 2) umma_gemm_kernel(
+    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M,
+    int N, int K, Epilogue ep, float* partial, int* err_word)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + kStages * kStageBytes);
+    uint64_t* empty = full + kStages;
+    uint64_t* accum = empty + kStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+    const int nk_all = K / BK, S = gridDim.z, z = blockIdx.z;
     const int kt0 = (int)((int64_t)nk_all * z / S), kt1 = (int)((int64_t)nk_all * (z + 1) / S);
-    const int nk = kt1 - kt0;
-    load_stage(0, kt0 * TK);
-    const int r8 = lane & 7, j4 = lane >> 3;
-    for (int kt = 0; kt < nk; ++kt) {
-        const int st = kt & 1;
-        if (kt + 1 < nk) {
-            load_stage(st ^ 1, (kt0 + kt + 1) * TK);
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
-        } else {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < TK; kk += 16) {
-            uint32_t a[4][4], b[2][4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int mb = wm * 64 + i * 16;
-                if (AK) ldsm_x4(a[i], &As[st][mb + r8 + 8 * (j4 & 1)][kk + 8 * (j4 >> 1)]);
-                else ldsm_x4_t(a[i], &As[st][kk + r8 + 8 * (j4 >> 1)][mb + 8 * (j4 & 1)]);
-            }
-#pragma unroll
-            for (int jp = 0; jp < 2; ++jp) {
-                const int nb = wn * 32 + jp * 16;
-                if (BKC) ldsm_x4(b[jp], &Bs[st][nb + r8 + 8 * (j4 >> 1)][kk + 8 * (j4 & 1)]);
-                else ldsm_x4_t(b[jp], &Bs[st][kk + r8 + 8 * (j4 & 1)][nb + 8 * (j4 >> 1)]);
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    mma_bf16(acc[i][j], a[i], b[j >> 1][2 * (j & 1)], b[j >> 1][2 * (j & 1) + 1]);
-        }
-        __syncthreads();
-    }
+    const int nk = kt1 - kt0;   // >= 1 (the host keeps every slice non-empty)
 
-    if (partial) {   // split K: raw partial sums of slice z, epilogue in splitk_reduce
-        float* P = partial + (size_t)z * M * N;
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-#pragma unroll
-                for (int hlf = 0; hlf < 2; ++hlf) {
-                    const int m = m0 + wm * 64 + i * 16 + (lane >> 2) + 8 * hlf;
-                    const int n = n0 + wn * 32 + j * 8 + 2 * (lane & 3);
-                    *reinterpret_cast<float2*>(P + (size_t)m * N + n) =
-                        make_float2(acc[i][j][2 * hlf], acc[i][j][2 * hlf + 1]);
-                }
-        return;
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            rad::mbar_init(&full[s], 1);
+            rad::mbar_init(&empty[s], 1);
+        }
+        rad::mbar_init(accum, 1);
+        *abort_flag = 0;
+        rad::fence_mbar_init();
     }
-    // epilogue
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // ---- producer: TMA loads, kStages deep
+        int issued = 0;
+        for (int kt = 0; kt < nk; ++kt) {
+            const int s = kt % kStages;
+            const uint32_t u = (uint32_t)(kt / kStages);
+            if (kt >= kStages &&
+                !rad::mbar_wait_bounded(&empty[s], (u - 1) & 1, abort_flag, err_word))
+                break;
+            rad::mbar_arrive_expect_tx(&full[s], kStageBytes);
+            unsigned char* st = base + s * kStageBytes;
+            tma_load_2d(st, &tmA, (kt0 + kt) * BK, m0, &full[s]);
+            tma_load_2d(st + kTileBytes, &tmB, (kt0 + kt) * BK, n0, &full[s]);
+            ++issued;
+        }
+        if (*abort_flag) {
+            // never leave with a copy in flight: wait (bounded) for the last
+            // kStages issued loads to land
+            for (int kt = issued > kStages ? issued - kStages : 0; kt < issued; ++kt)
+                rad::mbar_drain(&full[kt % kStages], (uint32_t)(kt / kStages) & 1);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer
+        bool ok = true;
+        for (int kt = 0; kt < nk && ok; ++kt) {
+            const int s = kt % kStages;
+            const uint32_t u = (uint32_t)(kt / kStages);
+            if (!rad::mbar_wait_bounded(&full[s], u & 1, abort_flag, err_word)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t a0 = smem_addr(base + s * kStageBytes);
+            const uint32_t b0 = a0 + kTileBytes;
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+            for (int kk = 0; kk < BK / 16; ++kk)
+                umma_bf16(tmem, sw128_desc(a0 + 32 * kk), sw128_desc(b0 + 32 * kk),
+                          (kt > 0 || kk > 0) ? 1u : 0u);
+            umma_commit(&empty[s]);
+        }
+        // the accumulator barrier completes once every MMA issued above is done
+        // (also after an abort, so the epilogue's drain below always ends)
+        umma_commit(accum);
+    }
+    __syncwarp();
+
+    // ---- epilogue: warp w owns accumulator rows (TMEM lanes) 32 w .. 32 w + 31.
+    // Each 32 x 32 block goes TMEM -> registers (one row per lane) -> shared
+    // memory (the drained pipeline buffers; float4 slots XOR-swizzled by row,
+    // conflict-free both ways) -> registers (four consecutive columns per
+    // lane, eight lanes per row), so every global access of a warp covers four
+    // whole 128-byte row segments.
+    const bool ready = rad::mbar_wait_bounded(accum, 0, abort_flag, err_word);
+    if (!ready) rad::mbar_drain(accum, 0);
+    __syncwarp();     // tcgen05.ld below is warp-collective
+    tc_fence_after();
+    const bool live = ready && !*abort_flag;
+    float* stage = reinterpret_cast<float*>(base) + warp * 32 * 32;
+    const int qi = lane & 7, ri = lane >> 3;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        float4* srow = reinterpret_cast<float4*>(stage + lane * 32);
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int hlf = 0; hlf < 2; ++hlf) {
-                const int m = m0 + wm * 64 + i * 16 + (lane >> 2) + 8 * hlf;
-                const int n = n0 + wn * 32 + j * 8 + 2 * (lane & 3);
-                float v0 = acc[i][j][2 * hlf], v1 = acc[i][j][2 * hlf + 1];
+        for (int j = 0; j < 8; ++j)
+            srow[j ^ (lane & 7)] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        __syncwarp();
+        if (live) {
+#pragma unroll 2
+            for (int k = 0; k < 8; ++k) {
+                const int r = 4 * k + ri;
+                float4 x = reinterpret_cast<const float4*>(stage + r * 32)[qi ^ (r & 7)];
+                const int n = n0 + c0 + 4 * qi;
+                const size_t o = (size_t)(m0 + warp * 32 + r) * N + n;
+                if (partial) {
+                    *reinterpret_cast<float4*>(partial + (size_t)z * M * N + o) = x;
+                    continue;
+                }
                 if (ep.bias) {
-                    v0 += ep.bias[n];
-                    v1 += ep.bias[n + 1];
+                    const float4 b = *reinterpret_cast<const float4*>(ep.bias + n);
+                    x.x += b.x;
+                    x.y += b.y;
+                    x.z += b.z;
+                    x.w += b.w;
                 }
-                const size_t o = (size_t)m * N + n;
                 if (ep.mask) {
-                    v0 = ep.mask[o] > 0.0f ? v0 : 0.0f;
-                    v1 = ep.mask[o + 1] > 0.0f ? v1 : 0.0f;
+                    const float4 q = *reinterpret_cast<const float4*>(ep.mask + o);
+                    x.x = q.x > 0.0f ? x.x : 0.0f;
+                    x.y = q.y > 0.0f ? x.y : 0.0f;
+                    x.z = q.z > 0.0f ? x.z : 0.0f;
+                    x.w = q.w > 0.0f ? x.w : 0.0f;
                 }
-                if (ep.out_f32) *reinterpret_cast<float2*>(ep.out_f32 + o) = make_float2(v0, v1);
+                if (ep.out_f32) *reinterpret_cast<float4*>(ep.out_f32 + o) = x;
                 if (ep.out_bf16) {
                     if (ep.relu) {
-                        v0 = fmaxf(v0, 0.0f);
-                        v1 = fmaxf(v1, 0.0f);
+                        x.x = fmaxf(x.x, 0.0f);
+                        x.y = fmaxf(x.y, 0.0f);
+                        x.z = fmaxf(x.z, 0.0f);
+                        x.w = fmaxf(x.w, 0.0f);
                     }
-                    *reinterpret_cast<__nv_bfloat162*>(ep.out_bf16 + o) = __floats2bfloat162_rn(v0, v1);
+                    const __nv_bfloat162 lo = __floats2bfloat162_rn(x.x, x.y);
+                    const __nv_bfloat162 hi = __floats2bfloat162_rn(x.z, x.w);
+                    *reinterpret_cast<uint2*>(ep.out_bf16 + o) =
+                        make_uint2(*reinterpret_cast<const uint32_t*>(&lo),
+                                   *reinterpret_cast<const uint32_t*>(&hi));
                 }
             }
+        }
+        __syncwarp();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols)
+                     : "memory");
 }
 
 // Sum of the S slices' partials in slice order, then the epilogue of the
@@ -254,23 +371,102 @@ __global__ void splitk_reduce(const float* __restrict__ partial, int S, int M, i
     }
 }
 
-// C = op(A) op(B) with the fused epilogue.  work: FP32 scratch of at least
-// split_count(M, N, K) * M * N floats, or null to run unsplit.
-template <bool AK, bool BKC>
-cudaError_t gemm(const bf16* A, const bf16* B, int M, int N, int K, int lda, int ldb,
-                 const Epilogue& ep, cudaStream_t st, float* work = nullptr)
+// out [cols][rows] = in [rows][cols]^T (BF16), 32 x 32 tiles through shared memory.
+__global__ void transpose_bf16(const bf16* __restrict__ in, bf16* __restrict__ out, int rows,
+                               int cols)
 {
-    if (M % TM || N % TN || K % TK || lda % 8 || ldb % 8) return cudaErrorInvalidValue;
+    __shared__ bf16 t[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) t[i][threadIdx.x] = in[(size_t)r * cols + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) out[(size_t)c * rows + r] = t[threadIdx.x][i];
+    }
+}
+
+cudaError_t transpose(const bf16* in, bf16* out, int rows, int cols, cudaStream_t st)
+{
+    dim3 grid((cols + 31) / 32, (rows + 31) / 32), block(32, 8);
+    transpose_bf16<<<grid, block, 0, st>>>(in, out, rows, cols);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) fail(RAD_MLP_ECUDA, "transpose: launch", e);
+    return e;
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// Row-major BF16 [rows][ld] viewed as rows x cols, K (= cols) innermost; box
+// 64 x 128, 128-byte swizzle.
+bool make_map(CUtensorMap* map, const bf16* ptr, int rows, int cols, int ld)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(bf16)};
+    const cuuint32_t box[2] = {BK, BM};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(ptr), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// C [M][N] = A [M][K] B [N][K]^T with the fused epilogue.  work: FP32 scratch
+// of at least split_count(M, N, K) * M * N floats, or null to run unsplit.
+cudaError_t gemm_tn(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K,
+                    const Epilogue& ep, cudaStream_t st, float* work, int* err_word)
+{
+    if (M % BM || N % BN || K % BK || K < BK || lda % 8 || ldb % 8 || lda < K || ldb < K ||
+        (reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) % 16 || !err_word) {
+        fail(RAD_MLP_EINVAL, "gemm: shape, leading dimension or alignment not supported");
+        return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaFuncSetAttribute(umma_gemm_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kGemmSmem);
+    if (e != cudaSuccess) {
+        fail(RAD_MLP_ECUDA, "gemm: shared-memory attribute", e);
+        return e;
+    }
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, A, M, K, lda) || !make_map(&mb, B, N, K, ldb)) {
+        fail(RAD_MLP_EINVAL, "gemm: tensor map encoding failed");
+        return cudaErrorInvalidValue;
+    }
     const int S = work ? split_count(M, N, K) : 1;
-    dim3 grid(N / TN, M / TM, S);
-    gemm_bf16_kernel<AK, BKC><<<grid, kGemmThreads, 0, st>>>(A, B, M, N, K, lda, ldb, ep,
-                                                             S > 1 ? work : nullptr);
+    dim3 grid(N / BN, M / BM, S);
+    umma_gemm_kernel<<<grid, kGemmThreads, kGemmSmem, st>>>(ma, mb, M, N, K, ep,
+                                                           S > 1 ? work : nullptr, err_word);
     if (S > 1) {
         const int64_t n4 = (int64_t)M * N / 4;
         const int blocks = (int)std::min<int64_t>((n4 + 255) / 256, 4 * 152);
         splitk_reduce<<<blocks, 256, 0, st>>>(work, S, M, N, ep);
     }
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) fail(RAD_MLP_ECUDA, "gemm: launch", e);
+    return e;
 }
 
 __global__ void to_bf16_rows(const float* x, bf16* y, int rows_valid, int rows, int cols)
@@ -362,7 +558,8 @@ struct rad_mlp {
     cudaStream_t st = nullptr;
     // parameters: per layer, [out][in]
     std::vector<float*> W, b, Wm, Wv, bm, bv, dW, db;
-    std::vector<bf16*> Wb;
+    std::vector<bf16*> Wb;          // BF16 copy of W [out][in] (forward operand)
+    std::vector<bf16*> Wbt;         // BF16 copy of W^T [in][out] (input-gradient operand)
     int64_t step = 0;
     // activations: h[l] bf16 [rows][w[l]] (h[0] = input), z[l] fp32 [rows][w[l]] (l >= 1)
     std::vector<bf16*> h;
@@ -373,11 +570,17 @@ struct rad_mlp {
     double* loss = nullptr;
     float* xin = nullptr;           // staging for host inputs [rows][w[0]]
     float* work = nullptr;          // split-K partial sums (largest split product)
+    bf16* gt = nullptr;             // G^T [w][rows] for the weight gradient (largest layer)
+    bf16* ht = nullptr;             // H^T [w][rows]
+    int* err = nullptr;             // GEMM timeout word
 };
 
-#define MCU(call)                                            \
-    do {                                                     \
-        if ((call) != cudaSuccess) return RAD_MLP_ECUDA;     \
+#define MCU(call)                                                                  \
+    do {                                                                           \
+        const cudaError_t e_ = (call);                                             \
+        if (e_ != cudaSuccess)                                                     \
+            return e_ == cudaErrorInvalidValue ? fail(RAD_MLP_EINVAL, #call, e_)   \
+                                               : fail(RAD_MLP_ECUDA, #call, e_);   \
     } while (0)
 
 static int round128(int n) { return (n + 127) / 128 * 128; }
@@ -411,6 +614,7 @@ int rad_mlp_init(rad_mlp** out, const int32_t* widths, int32_t n_layers, int32_t
     m->W.assign(n_layers, nullptr);
     m->b = m->Wm = m->Wv = m->bm = m->bv = m->dW = m->db = m->W;
     m->Wb.assign(n_layers, nullptr);
+    m->Wbt.assign(n_layers, nullptr);
     m->h.assign(n_layers + 1, nullptr);
     m->z.assign(n_layers + 1, nullptr);
     m->gb.assign(n_layers + 1, nullptr);
@@ -421,6 +625,7 @@ int rad_mlp_init(rad_mlp** out, const int32_t* widths, int32_t n_layers, int32_t
         MAL(m->Wv[l], np * 4);
         MAL(m->dW[l], np * 4);
         MAL(m->Wb[l], np * 2);
+        MAL(m->Wbt[l], np * 2);
         MAL(m->b[l], (size_t)m->w[l + 1] * 4);
         MAL(m->bm[l], (size_t)m->w[l + 1] * 4);
         MAL(m->bv[l], (size_t)m->w[l + 1] * 4);
@@ -448,7 +653,13 @@ int rad_mlp_init(rad_mlp** out, const int32_t* widths, int32_t n_layers, int32_t
         }
     }
     MAL(m->work, work * 4);
+    int wmax = 0;
+    for (int l = 0; l <= n_layers; ++l) wmax = std::max(wmax, m->w[l]);
+    MAL(m->gt, (size_t)wmax * R * 2);
+    MAL(m->ht, (size_t)wmax * R * 2);
 #undef MAL
+    m->err = gemm_err_word();
+    if (!m->err) return bail(RAD_MLP_ECUDA);
     if (cudaDeviceSynchronize() != cudaSuccess) return bail(RAD_MLP_ECUDA);
     *out = m;
     return RAD_MLP_OK;
@@ -462,6 +673,7 @@ int rad_mlp_set_layer(rad_mlp* m, int32_t layer, const float* W, const float* b)
     MCU(cudaMemcpyAsync(m->b[layer], b, (size_t)m->w[layer + 1] * 4, cudaMemcpyDefault, m->st));
     f32_to_bf16<<<grid_for(np), 256, 0, m->st>>>(m->W[layer], m->Wb[layer], (int64_t)np);
     MCU(cudaGetLastError());
+    MCU(transpose(m->Wb[layer], m->Wbt[layer], m->w[layer + 1], m->w[layer], m->st));
     // a new parameter set restarts the optimiser
     MCU(cudaMemsetAsync(m->Wm[layer], 0, np * 4, m->st));
     MCU(cudaMemsetAsync(m->Wv[layer], 0, np * 4, m->st));
@@ -499,8 +711,8 @@ static int forward(rad_mlp* m, int32_t batch, const float* x)
         const bool last = l == m->L - 1;
         Epilogue ep{m->b[l], nullptr, m->z[l + 1], last ? nullptr : m->h[l + 1], 1};
         // z = h W^T + b: A = h [R][in], B = W [out][in]
-        MCU((gemm<true, true>(m->h[l], m->Wb[l], R, m->w[l + 1], m->w[l], m->w[l], m->w[l], ep, m->st,
-                              m->work)));
+        MCU(gemm_tn(m->h[l], m->w[l], m->Wb[l], m->w[l], R, m->w[l + 1], m->w[l], ep, m->st,
+                    m->work, m->err));
     }
     return RAD_MLP_OK;
 }
@@ -512,7 +724,7 @@ int rad_mlp_forward(rad_mlp* m, int32_t batch, const float* x, float* y)
     if (rc) return rc;
     MCU(cudaMemcpyAsync(y, m->z[m->L], (size_t)batch * m->w[m->L] * 4, cudaMemcpyDefault, m->st));
     MCU(cudaStreamSynchronize(m->st));
-    return RAD_MLP_OK;
+    return gemm_timed_out() ? RAD_MLP_ETIMEOUT : RAD_MLP_OK;
 }
 
 int rad_mlp_gradients(rad_mlp* m, int32_t batch, const float* x, const float* t, double* loss)
@@ -529,9 +741,12 @@ int rad_mlp_gradients(rad_mlp* m, int32_t batch, const float* x, const float* t,
     MCU(cudaGetLastError());
     for (int l = L - 1; l >= 0; --l) {
         const int in = m->w[l], outw = m->w[l + 1];
-        // dW = G^T H: A = G stored [R][out] (M = out contiguous), B = H stored [R][in]
+        // dW = G^T H over the batch: both operands transposed to batch-contiguous
+        // copies, G^T [out][R] and H^T [in][R]
         Epilogue ew{nullptr, nullptr, m->dW[l], nullptr, 0};
-        MCU((gemm<false, false>(m->gb[l + 1], m->h[l], outw, in, R, outw, in, ew, m->st)));
+        MCU(transpose(m->gb[l + 1], m->gt, R, outw, m->st));
+        MCU(transpose(m->h[l], m->ht, R, in, m->st));
+        MCU(gemm_tn(m->gt, R, m->ht, R, outw, in, R, ew, m->st, nullptr, m->err));
         // db of the output layer: column sums of the FP32 output gradient (the
         // hidden layers' bias gradients follow below, from the FP32 masked products)
         if (l == L - 1) {
@@ -539,11 +754,11 @@ int rad_mlp_gradients(rad_mlp* m, int32_t batch, const float* x, const float* t,
             MCU(cudaGetLastError());
         }
         if (l > 0) {
-            // G_prev = (G W) * [z_l > 0]: A = G [R][out] (K = out contiguous), B = W [out][in]
-            // stored [K][N]; the FP32 product lands in z_l's buffer for the bias sum
+            // G_prev = (G W) * [z_l > 0]: A = G [R][out], B = W^T [in][out] (both
+            // out-contiguous); the FP32 product lands in z_l's buffer for the bias sum
             Epilogue eg{nullptr, m->z[l], m->z[l], m->gb[l], 0};
-            MCU((gemm<true, false>(m->gb[l + 1], m->Wb[l], R, in, outw, outw, in, eg, m->st,
-                                   m->work)));
+            MCU(gemm_tn(m->gb[l + 1], outw, m->Wbt[l], outw, R, in, outw, eg, m->st, m->work,
+                        m->err));
         }
     }
     // bias gradients of the hidden layers: column sums of the FP32 masked products
@@ -553,7 +768,7 @@ int rad_mlp_gradients(rad_mlp* m, int32_t batch, const float* x, const float* t,
     }
     if (loss) MCU(cudaMemcpyAsync(loss, m->loss, sizeof(double), cudaMemcpyDeviceToHost, m->st));
     MCU(cudaStreamSynchronize(m->st));
-    return RAD_MLP_OK;
+    return gemm_timed_out() ? RAD_MLP_ETIMEOUT : RAD_MLP_OK;
 }
 
 int rad_mlp_adam(rad_mlp* m, float lr, float beta1, float beta2, float eps)
@@ -567,6 +782,7 @@ int rad_mlp_adam(rad_mlp* m, float lr, float beta1, float beta2, float eps)
         const int64_t np = (int64_t)m->w[l + 1] * m->w[l];
         adam_update<<<grid_for(np), 256, 0, m->st>>>(m->W[l], m->Wb[l], m->Wm[l], m->Wv[l], m->dW[l],
                                                      np, lr, beta1, beta2, eps, c1, c2);
+        MCU(transpose(m->Wb[l], m->Wbt[l], m->w[l + 1], m->w[l], m->st));
         adam_update<<<grid_for(m->w[l + 1]), 256, 0, m->st>>>(m->b[l], nullptr, m->bm[l], m->bv[l],
                                                               m->db[l], m->w[l + 1], lr, beta1,
                                                               beta2, eps, c1, c2);
@@ -575,31 +791,53 @@ int rad_mlp_adam(rad_mlp* m, float lr, float beta1, float beta2, float eps)
     return RAD_MLP_OK;
 }
 
-int rad_mlp_gemm(int32_t AK, int32_t BK, int32_t M, int32_t N, int32_t K, const void* A,
-                      const void* B, float* C)
+int rad_mlp_gemm(int32_t a_kcontig, int32_t b_kcontig, int32_t M, int32_t N, int32_t K, const void* A,
+                 const void* B, float* C)
 {
-    if (M < 1 || N < 1 || K < 1 || M % TM || N % TN || K % TK || !A || !B || !C)
-        return RAD_MLP_EINVAL;
+    if (M < 1 || N < 1 || K < 1 || M % BM || N % BN || K % BK || !A || !B || !C)
+        return fail(RAD_MLP_EINVAL, "rad_mlp_gemm: M, N must be multiples of 128 and K of 64");
+    int* err = gemm_err_word();
+    if (!err) return fail(RAD_MLP_ECUDA, "rad_mlp_gemm: error word");
     Epilogue ep{nullptr, nullptr, C, nullptr, 0};
     const bf16* a = static_cast<const bf16*>(A);
     const bf16* b = static_cast<const bf16*>(B);
-    // split-K scratch from the stream-ordered pool of the default stream
-    float* work = nullptr;
+    // scratch from the default stream's stream-ordered pool: split-K partials
+    // and K-contiguous copies of operands stored the other way round
     const int S = split_count(M, N, K);
-    if (S > 1 && cudaMallocAsync(&work, (size_t)S * M * N * 4, nullptr) != cudaSuccess) {
-        cudaGetLastError();
-        return RAD_MLP_ENOMEM;
+    const size_t part = S > 1 ? (size_t)S * M * N * 4 : 0;
+    const size_t at = a_kcontig ? 0 : (size_t)M * K * 2, bt = b_kcontig ? 0 : (size_t)N * K * 2;
+    unsigned char* scratch = nullptr;
+    if (part + at + bt &&
+        cudaMallocAsync(reinterpret_cast<void**>(&scratch), part + at + bt, nullptr) != cudaSuccess) {
+        return fail(RAD_MLP_ENOMEM, "rad_mlp_gemm: scratch", cudaGetLastError());
     }
-    cudaError_t e;
-    const int lda = AK ? K : M, ldb = BK ? K : N;
-    if (AK && BK) e = gemm<true, true>(a, b, M, N, K, lda, ldb, ep, nullptr, work);
-    else if (AK) e = gemm<true, false>(a, b, M, N, K, lda, ldb, ep, nullptr, work);
-    else if (BK) e = gemm<false, true>(a, b, M, N, K, lda, ldb, ep, nullptr, work);
-    else e = gemm<false, false>(a, b, M, N, K, lda, ldb, ep, nullptr, work);
-    if (work) cudaFreeAsync(work, nullptr);
+    float* work = part ? reinterpret_cast<float*>(scratch) : nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!a_kcontig) {       // A stored [K][M]
+        bf16* t = reinterpret_cast<bf16*>(scratch + part);
+        e = transpose(a, t, K, M, nullptr);
+        a = t;
+    }
+    if (e == cudaSuccess && !b_kcontig) {       // B stored [K][N]
+        bf16* t = reinterpret_cast<bf16*>(scratch + part + at);
+        e = transpose(b, t, K, N, nullptr);
+        b = t;
+    }
+    if (e == cudaSuccess) e = gemm_tn(a, K, b, K, M, N, K, ep, nullptr, work, err);
+    if (scratch) cudaFreeAsync(scratch, nullptr);
     if (e == cudaErrorInvalidValue) return RAD_MLP_EINVAL;
     return e == cudaSuccess ? RAD_MLP_OK : RAD_MLP_ECUDA;
 }
+
+int rad_mlp_check(void)
+{
+    const cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail(RAD_MLP_ECUDA, "rad_mlp_check", e);
+    return gemm_timed_out() ? fail(RAD_MLP_ETIMEOUT, "a GEMM block's bounded wait expired")
+                            : RAD_MLP_OK;
+}
+
+const char* rad_mlp_last_error(void) { return g_last_error; }
 
 void rad_mlp_destroy(rad_mlp* m)
 {
@@ -608,10 +846,11 @@ void rad_mlp_destroy(rad_mlp* m)
     for (auto* vv : {&m->W, &m->b, &m->Wm, &m->Wv, &m->bm, &m->bv, &m->dW, &m->db, &m->z})
         for (float* p : *vv)
             if (p) cudaFree(p);
-    for (auto* vv : {&m->Wb, &m->h, &m->gb})
+    for (auto* vv : {&m->Wb, &m->Wbt, &m->h, &m->gb})
         for (bf16* p : *vv)
             if (p) cudaFree(p);
-    for (void* p : {(void*)m->t, (void*)m->g, (void*)m->loss, (void*)m->xin, (void*)m->work})
+    for (void* p : {(void*)m->t, (void*)m->g, (void*)m->loss, (void*)m->xin, (void*)m->work,
+                    (void*)m->gt, (void*)m->ht})
         if (p) cudaFree(p);
     delete m;
 }

@@ -9,7 +9,8 @@ from . import rad as _rad
 
 RAD_MLP_OK = 0
 EXPORTED = ("rad_mlp_init", "rad_mlp_set_layer", "rad_mlp_get_layer", "rad_mlp_forward",
-            "rad_mlp_gradients", "rad_mlp_adam", "rad_mlp_gemm", "rad_mlp_destroy")
+            "rad_mlp_gradients", "rad_mlp_adam", "rad_mlp_gemm", "rad_mlp_check",
+            "rad_mlp_last_error", "rad_mlp_destroy")
 
 
 def _lib():
@@ -33,6 +34,10 @@ def _lib():
                                      ctypes.c_float]
         lib.rad_mlp_gemm.restype = ctypes.c_int
         lib.rad_mlp_gemm.argtypes = [ctypes.c_int32] * 5 + [vp, vp, vp]
+        lib.rad_mlp_check.restype = ctypes.c_int
+        lib.rad_mlp_check.argtypes = []
+        lib.rad_mlp_last_error.restype = ctypes.c_char_p
+        lib.rad_mlp_last_error.argtypes = []
         lib.rad_mlp_destroy.restype = None
         lib.rad_mlp_destroy.argtypes = [vp]
         lib._mlp_bound = True
@@ -65,7 +70,7 @@ class MLP:
 
     def _chk(self, rc, what):
         if rc != RAD_MLP_OK:
-            raise RuntimeError(f"{what} failed ({rc})")
+            raise RuntimeError(f"{what} failed ({rc}): {last_error()}")
 
     @property
     def n_layers(self):
@@ -125,9 +130,21 @@ class MLP:
 
 
 def gemm(A, B, M, N, K, a_kcontig, b_kcontig, C):
-    """C (FP32, device) = op(A) op(B) on the tensor cores; A, B BF16 device tensors."""
+    """C (FP32, device) = op(A) op(B) on the tensor cores; A, B BF16 device tensors
+    (M, N multiples of 128, K of 64).  Enqueued on the default stream."""
     rc = _lib().rad_mlp_gemm(1 if a_kcontig else 0, 1 if b_kcontig else 0, M, N, K,
                              A.data_ptr(), B.data_ptr(), C.data_ptr())
     if rc != RAD_MLP_OK:
-        raise RuntimeError(f"rad_mlp_gemm failed ({rc})")
+        raise RuntimeError(f"rad_mlp_gemm failed ({rc}): {last_error()}")
     return C
+
+
+def check():
+    """Waits for the device; raises if a GEMM block's bounded wait expired."""
+    rc = _lib().rad_mlp_check()
+    if rc != RAD_MLP_OK:
+        raise RuntimeError(f"rad_mlp_check failed ({rc}): {last_error()}")
+
+
+def last_error():
+    return _lib().rad_mlp_last_error().decode(errors="replace")

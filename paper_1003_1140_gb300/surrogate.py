@@ -226,29 +226,52 @@ def errors(pred, true):
 
 def gemm_bench(batch=128, reps=20):
     """Tensor-core throughput of the network's three GEMM shapes at the workload's
-    size (forward X W^T, input gradient G W, weight gradient G^T X of the
-    512 x 393,216 output layer), CUDA-event timed."""
+    size, with the operands laid out as the training step holds them (all
+    K-contiguous): forward X W^T, input gradient G (W^T)^T and weight gradient
+    G^T H of the 512 x 393,216 output layer; then one whole training step
+    (forward, backward, Adam) of the surrogate network.  CUDA-event timed."""
     import torch
     from . import mlp as M
     K, N = 512, 393216
     res = {}
-    shapes = {"forward": (True, True, batch, N, K), "input_grad": (True, False, batch, K, N),
-              "weight_grad": (False, False, N, K, batch)}
-    for name, (ak, bk, m, n, k) in shapes.items():
-        A = torch.randn((m, k) if ak else (k, m), device="cuda").to(torch.bfloat16)
-        B = torch.randn((n, k) if bk else (k, n), device="cuda").to(torch.bfloat16)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    shapes = {"forward": (batch, N, K), "input_grad": (batch, K, N), "weight_grad": (N, K, batch)}
+    for name, (m, n, k) in shapes.items():
+        A = torch.randn((m, k), device="cuda").to(torch.bfloat16)
+        B = torch.randn((n, k), device="cuda").to(torch.bfloat16)
         C = torch.empty((m, n), dtype=torch.float32, device="cuda")
         for _ in range(3):
-            M.gemm(A, B, m, n, k, ak, bk, C)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            M.gemm(A, B, m, n, k, True, True, C)
+        M.check()
+        e0, e1 = ev(), ev()
         e0.record()
         for _ in range(reps):
-            M.gemm(A, B, m, n, k, ak, bk, C)
+            M.gemm(A, B, m, n, k, True, True, C)
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
         res[name] = {"M": m, "N": n, "K": k, "ms": ms, "tflops": 2.0 * m * n * k / (ms * 1e-3) / 1e12}
+        del A, B, C
+    M.check()
+    widths = [768, 512, 512, 512, N]
+    net = M.MLP(widths, batch)
+    net.init_params(0)
+    x = torch.randn((batch, widths[0]), device="cuda")
+    t = torch.randn((batch, widths[-1]), device="cuda")
+    for _ in range(3):
+        net.train_step(x, t, 1e-4)
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record()
+    for _ in range(reps):
+        net.train_step(x, t, 1e-4)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    flop = sum(2.0 * batch * widths[l] * widths[l + 1] for l in range(len(widths) - 1))
+    res["train_step"] = {"batch": batch, "ms": ms,
+                         "gemm_tflops": (3 * flop - 2.0 * batch * widths[0] * widths[1]) / (ms * 1e-3) / 1e12}
+    net.close()
     return res
 
 

@@ -17,13 +17,14 @@ def _bf16_dev(a):
 def test_gemm_layouts(ak, bk):
     from paper_1003_1140_gb300 import mlp
     rng = np.random.default_rng(2)
-    M, N, K = 256, 384, 160
+    M, N, K = 256, 384, 192
     A = ref.bf16(rng.normal(size=(M, K)))          # op(A) [M][K]
     B = ref.bf16(rng.normal(size=(N, K)))          # op(B)^T [N][K]
     Ad = _bf16_dev(A if ak else A.T.copy())
     Bd = _bf16_dev(B if bk else B.T.copy())
     C = torch.empty((M, N), dtype=torch.float32, device="cuda")
     mlp.gemm(Ad, Bd, M, N, K, ak, bk, C)
+    mlp.check()
     exp = A @ B.T
     got = C.cpu().numpy()
     assert np.abs(got - exp).max() <= 1e-4 * np.abs(exp).max()
@@ -31,11 +32,11 @@ def test_gemm_layouts(ak, bk):
 
 @pytest.mark.parametrize("ak,bk", [(True, False), (False, True)])
 def test_gemm_split_k(ak, bk):
-    """Two output tiles over K = 32 x 331: the product splits K into 41 slices
-    of 8 or 9 tiles (ragged), reduced in a fixed order."""
+    """Two output tiles over K = 64 x 331: the product splits K into 82 slices
+    of 4 or 5 tiles (ragged), reduced in a fixed order."""
     from paper_1003_1140_gb300 import mlp
     rng = np.random.default_rng(5)
-    M, N, K = 128, 256, 32 * 331
+    M, N, K = 128, 256, 64 * 331
     A = ref.bf16(rng.normal(size=(M, K)))
     B = ref.bf16(rng.normal(size=(N, K)))
     Ad = _bf16_dev(A if ak else A.T.copy())
@@ -44,6 +45,7 @@ def test_gemm_split_k(ak, bk):
     mlp.gemm(Ad, Bd, M, N, K, ak, bk, C)
     C2 = torch.empty_like(C)
     mlp.gemm(Ad, Bd, M, N, K, ak, bk, C2)
+    mlp.check()
     exp = A @ B.T
     got = C.cpu().numpy()
     # FP32 accumulation of 10,592 products of unit normals: |error| ~ sqrt(K) 2^-24 max|partial|
