@@ -479,28 +479,75 @@ __global__ void to_bf16_rows(const float* x, bf16* y, int rows_valid, int rows, 
     }
 }
 
-// MSE over the valid rows: g = 2 (y - t) / (rows_valid * cols) (FP32 and BF16),
-// loss accumulated in FP64.
-__global__ void mse_grad(const float* y, const float* t, float* g, bf16* gb, double* loss,
-                         int rows_valid, int rows, int cols)
+// MSE over the valid rows, loss = sum (y - t)^2 / (rows_valid * cols), and its
+// gradient g = 2 (y - t) / (rows_valid * cols) (FP32 and BF16; zero on padded rows).
+// In 32 x 32 tiles, also writing BF16 G^T [cols][rows]
+// (the weight-gradient operand) through shared memory; each block's share of
+// the loss (FP32 within the block) goes to part[block] and is summed in FP64,
+// in a fixed order, by loss_sum.
+__global__ void __launch_bounds__(256) mse_tile(const float* __restrict__ y,
+                                                const float* __restrict__ t,
+                                                float* __restrict__ g, bf16* __restrict__ gb,
+                                                bf16* __restrict__ gbt,
+                                                double* __restrict__ part, float scale,
+                                                int rows_valid, int rows, int cols)
 {
-    const int64_t n = (int64_t)rows * cols;
-    const double inv = 1.0 / ((double)rows_valid * cols);
-    double part = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(i / cols);
-        float gi = 0.0f;
-        if (r < rows_valid) {
-            const float d = y[i] - t[i];
-            part += (double)d * d;
-            gi = (float)(2.0 * inv) * d;
-        }
-        g[i] = gi;
-        gb[i] = __float2bfloat16_rn(gi);
+    // scale = 2 / (rows_valid * cols), rounded once on the host: this kernel
+    // issues no FP64 arithmetic (the FP64 pipe is 1/64 of FP32 here), only
+    // the per-block share is widened
+    __shared__ bf16 tr[32][33];
+    __shared__ float red[8];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32, c = c0 + threadIdx.x;
+    // rows threadIdx.y + 8 q of the tile: all loads first, then the stores
+    float d[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int r = r0 + threadIdx.y + 8 * q;
+        const size_t k = (size_t)r * cols + c;
+        d[q] = (r < rows_valid && c < cols) ? y[k] - t[k] : 0.0f;
     }
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
-    if ((threadIdx.x & 31) == 0 && part != 0.0) atomicAdd(loss, part * inv);
+    float acc = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = threadIdx.y + 8 * q, r = r0 + i;
+        const float gi = scale * d[q];
+        acc = fmaf(d[q], d[q], acc);
+        const bf16 h = __float2bfloat16_rn(gi);
+        if (r < rows && c < cols) {
+            const size_t k = (size_t)r * cols + c;
+            g[k] = gi;
+            gb[k] = h;
+        }
+        tr[i][threadIdx.x] = h;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) red[threadIdx.y] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        float b = 0.0f;
+        for (int w = 0; w < 8; ++w) b += red[w];
+        part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = (double)b;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = threadIdx.y + 8 * q, cc = c0 + i, r = r0 + threadIdx.x;
+        if (r < rows && cc < cols) gbt[(size_t)cc * rows + r] = tr[threadIdx.x][i];
+    }
+}
+
+// loss = sum of the n block shares / (rows_valid * cols), one block, fixed order.
+__global__ void loss_sum(const double* part, int64_t n, double inv, double* loss)
+{
+    __shared__ double red[256];
+    double a = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) a += part[i];
+    red[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = red[0] * inv;
 }
 
 // db[n] = sum over rows of g[r][n]
@@ -527,6 +574,56 @@ __global__ void adam_update(float* w, bf16* wb, float* m, float* v, const float*
         const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
         w[i] = wi;
         if (wb) wb[i] = __float2bfloat16_rn(wi);
+    }
+}
+
+// The same Adam step for a weight matrix W [rows][cols] in 32 x 32 tiles, also
+// writing the BF16 copy of W and, through shared memory, of W^T [cols][rows]:
+// one pass over the optimiser state instead of a second one for the transpose.
+__global__ void __launch_bounds__(256) adam_tile(float* __restrict__ w, bf16* __restrict__ wb,
+                                                 bf16* __restrict__ wbt, float* __restrict__ m,
+                                                 float* __restrict__ v,
+                                                 const float* __restrict__ g, int rows, int cols,
+                                                 float lr, float b1, float b2, float eps, float c1,
+                                                 float c2)
+{
+    __shared__ bf16 t[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    const int c = c0 + threadIdx.x;
+    // rows threadIdx.y + 8 q of the tile: all loads first, then the update
+    float gq[4], mq[4], vq[4], wq[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int r = r0 + threadIdx.y + 8 * q;
+        const bool in = r < rows && c < cols;
+        const size_t k = (size_t)r * cols + c;
+        gq[q] = in ? g[k] : 0.0f;
+        mq[q] = in ? m[k] : 0.0f;
+        vq[q] = in ? v[k] : 0.0f;
+        wq[q] = in ? w[k] : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = threadIdx.y + 8 * q, r = r0 + i;
+        const float gi = gq[q];
+        const float mi = b1 * mq[q] + (1.0f - b1) * gi;
+        const float vi = b2 * vq[q] + (1.0f - b2) * gi * gi;
+        const float wi = wq[q] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        const bf16 h = __float2bfloat16_rn(wi);
+        if (r < rows && c < cols) {
+            const size_t k = (size_t)r * cols + c;
+            m[k] = mi;
+            v[k] = vi;
+            w[k] = wi;
+            wb[k] = h;
+        }
+        t[i][threadIdx.x] = h;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = threadIdx.y + 8 * q, cc = c0 + i, r = r0 + threadIdx.x;
+        if (r < rows && cc < cols) wbt[(size_t)cc * rows + r] = t[threadIdx.x][i];
     }
 }
 
@@ -568,6 +665,7 @@ struct rad_mlp {
     float* g = nullptr;             // output gradient fp32 [rows][w[L]]
     std::vector<bf16*> gb;          // layer gradients bf16: gb[l] [rows][w[l]] for l >= 1
     double* loss = nullptr;
+    double* loss_part = nullptr;    // per-block loss shares of mse_tile
     float* xin = nullptr;           // staging for host inputs [rows][w[0]]
     float* work = nullptr;          // split-K partial sums (largest split product)
     bf16* gt = nullptr;             // G^T [w][rows] for the weight gradient (largest layer)
@@ -641,6 +739,7 @@ int rad_mlp_init(rad_mlp** out, const int32_t* widths, int32_t n_layers, int32_t
     MAL(m->t, (size_t)R * m->w[n_layers] * 4);
     MAL(m->g, (size_t)R * m->w[n_layers] * 4);
     MAL(m->loss, sizeof(double));
+    MAL(m->loss_part, (size_t)(R / 32) * ((m->w[n_layers] + 31) / 32) * sizeof(double));
     MAL(m->xin, (size_t)R * m->w[0] * 4);
     // split-K scratch: the forward and input-gradient products are R rows wide
     // (the weight gradient reduces over R itself and never splits)
@@ -734,17 +833,27 @@ int rad_mlp_gradients(rad_mlp* m, int32_t batch, const float* x, const float* t,
     int rc = forward(m, batch, x);
     if (rc) return rc;
     const int L = m->L, wo = m->w[L];
-    MCU(cudaMemcpyAsync(m->t, t, (size_t)batch * wo * 4, cudaMemcpyDefault, m->st));
-    MCU(cudaMemsetAsync(m->loss, 0, sizeof(double), m->st));
-    mse_grad<<<grid_for((int64_t)R * wo), 256, 0, m->st>>>(m->z[L], m->t, m->g, m->gb[L], m->loss,
-                                                           batch, R, wo);
-    MCU(cudaGetLastError());
+    // device targets are read in place (mse_tile touches only the batch's rows)
+    const float* td = t;
+    if (!is_dev(t)) {
+        MCU(cudaMemcpyAsync(m->t, t, (size_t)batch * wo * 4, cudaMemcpyHostToDevice, m->st));
+        td = m->t;
+    }
+    {
+        const dim3 grid((wo + 31) / 32, R / 32);
+        mse_tile<<<grid, dim3(32, 8), 0, m->st>>>(m->z[L], td, m->g, m->gb[L], m->gt, m->loss_part,
+                                                  (float)(2.0 / ((double)batch * wo)), batch, R,
+                                                  wo);
+        loss_sum<<<1, 256, 0, m->st>>>(m->loss_part, (int64_t)grid.x * grid.y,
+                                       1.0 / ((double)batch * wo), m->loss);
+        MCU(cudaGetLastError());
+    }
     for (int l = L - 1; l >= 0; --l) {
         const int in = m->w[l], outw = m->w[l + 1];
         // dW = G^T H over the batch: both operands transposed to batch-contiguous
         // copies, G^T [out][R] and H^T [in][R]
         Epilogue ew{nullptr, nullptr, m->dW[l], nullptr, 0};
-        MCU(transpose(m->gb[l + 1], m->gt, R, outw, m->st));
+        if (l < L - 1) MCU(transpose(m->gb[l + 1], m->gt, R, outw, m->st));   // output layer: mse_tile
         MCU(transpose(m->h[l], m->ht, R, in, m->st));
         MCU(gemm_tn(m->gt, R, m->ht, R, outw, in, R, ew, m->st, nullptr, m->err));
         // db of the output layer: column sums of the FP32 output gradient (the
@@ -779,10 +888,10 @@ int rad_mlp_adam(rad_mlp* m, float lr, float beta1, float beta2, float eps)
     const float c1 = 1.0f - std::pow(beta1, (float)m->step);
     const float c2 = 1.0f - std::pow(beta2, (float)m->step);
     for (int l = 0; l < m->L; ++l) {
-        const int64_t np = (int64_t)m->w[l + 1] * m->w[l];
-        adam_update<<<grid_for(np), 256, 0, m->st>>>(m->W[l], m->Wb[l], m->Wm[l], m->Wv[l], m->dW[l],
-                                                     np, lr, beta1, beta2, eps, c1, c2);
-        MCU(transpose(m->Wb[l], m->Wbt[l], m->w[l + 1], m->w[l], m->st));
+        const int rows = m->w[l + 1], cols = m->w[l];
+        adam_tile<<<dim3((cols + 31) / 32, (rows + 31) / 32), dim3(32, 8), 0, m->st>>>(
+            m->W[l], m->Wb[l], m->Wbt[l], m->Wm[l], m->Wv[l], m->dW[l], rows, cols, lr, beta1, beta2,
+            eps, c1, c2);
         adam_update<<<grid_for(m->w[l + 1]), 256, 0, m->st>>>(m->b[l], nullptr, m->bm[l], m->bv[l],
                                                               m->db[l], m->w[l + 1], lr, beta1,
                                                               beta2, eps, c1, c2);
@@ -849,7 +958,8 @@ void rad_mlp_destroy(rad_mlp* m)
     for (auto* vv : {&m->Wb, &m->Wbt, &m->h, &m->gb})
         for (bf16* p : *vv)
             if (p) cudaFree(p);
-    for (void* p : {(void*)m->t, (void*)m->g, (void*)m->loss, (void*)m->xin, (void*)m->work,
+    for (void* p : {(void*)m->t, (void*)m->g, (void*)m->loss, (void*)m->loss_part, (void*)m->xin,
+                    (void*)m->work,
                     (void*)m->gt, (void*)m->ht})
         if (p) cudaFree(p);
     delete m;
