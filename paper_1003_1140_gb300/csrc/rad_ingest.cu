@@ -14,9 +14,14 @@
 
 namespace rad {
 
-__device__ __forceinline__ double min_image(double d, double L)
+// Nearest periodic image of a displacement: d - L rint(d / L).  A particle
+// that did not cross the boundary has |d| <= L/2, where that is d itself
+// (rint(d / L) = +-0 exactly); only a crossing pays for the FP64 division,
+// which this GPU runs on its 1/64-rate FP64 pipe.  Same value in every case.
+__device__ __forceinline__ double min_image(double d, double L, double half_L)
 {
-    return L > 0.0 ? d - L * rint(d / L) : d;
+    if (!(L > 0.0) || fabs(d) <= half_L) return d;
+    return d - L * rint(d / L);
 }
 
 // Selector bits of a sample: box tests on the position as handed over, cone
@@ -55,7 +60,14 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestParams p)
     const int64_t tile = col / kTileP, pp = col % kTileP;
 
     double xp[3], rp[3], up[3], ra[3];
+    const double half_L = 0.5 * p.box_L;
     bool have_state = p.step0 > 0;
+    // ring slot, position in the anchor block and anchor block of the next
+    // sample m (nsub = 1), advanced by counters instead of 64-bit divisions
+    int64_t m_next = p.step0 > 0 ? p.step0 - 1 : 0;
+    // (nblk is 0 for an FP64 ring, which has no anchors)
+    int64_t slot_n = m_next % p.ring, kpos_n = m_next % p.K;
+    int64_t blk_n = p.nblk > 0 ? (m_next / p.K) % p.nblk : 0;
     if (have_state) {
         for (int c = 0; c < 3; ++c) {
             xp[c] = p.x_prev[c * nc + col];
@@ -99,11 +111,16 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestParams p)
             continue;
         }
         // unwrapped position of this call
-        for (int c = 0; c < 3; ++c) rn[c] = rp[c] + min_image(xn[c] - xp[c], p.box_L);
+        for (int c = 0; c < 3; ++c) rn[c] = rp[c] + min_image(xn[c] - xp[c], p.box_L, half_L);
 
         // sample m = s - 1: r_m = rp, u_{m-1/2} = up, u_{m+1/2} = un
         const int64_t m = s - 1;
-        const int64_t slot = m % p.ring;
+        const int64_t slot = slot_n, kpos = kpos_n, blk = blk_n;
+        if (++slot_n == p.ring) slot_n = 0;
+        if (++kpos_n == p.K) {
+            kpos_n = 0;
+            if (++blk_n == p.nblk) blk_n = 0;
+        }
         if (p.nsub > 1) {
             // Sub-cycling (Sec. 2.2: tracked particles sub-cycled at
             // dt_synth <= dt_sim / 10): n sub-samples per PIC sample at
@@ -184,8 +201,8 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestParams p)
             // and weakly parallel accelerations a frozen-field push produces.
             // anchor position r_a as an FP32 hi + lo pair; dr is taken relative
             // to exactly hi + lo, the value the accumulation kernel sees
-            float* an = p.anc32 + (tile * p.nblk + (m / p.K) % p.nblk) * (6 * kTileP) + pp;
-            if ((m % p.K) == 0) {
+            float* an = p.anc32 + (tile * p.nblk + blk) * (6 * kTileP) + pp;
+            if (kpos == 0) {
                 for (int c = 0; c < 3; ++c) {
                     const float hi = (float)rp[c];
                     const float lo = (float)(rp[c] - (double)hi);
