@@ -304,3 +304,62 @@ def config(k: int, scale_particles: float = 1.0) -> Workload:
                         0.05, healpix_centres(4), [log_grid(0.1, 1000.0, 2048)],
                         [(0, 2000, 1, 0)])
     raise ValueError("workloads are numbered 1..5")
+
+
+# ---------------------------------------------------------------------------
+# initial state of the live two-stream PIC (Sec. 2.1 setup)
+# ---------------------------------------------------------------------------
+@dataclass
+class TwoStream:
+    """Two equal-density neutral beams streaming against each other along
+    `axis` in a periodic 2D3V box of n x n cells of size d (Sec. 2.1: the
+    filamentation setup, with the paper's reduced mass ratio 64 for the
+    baryonic case, or pairs).  Every electron has a partner of the other
+    species at the same position with the same bulk momentum, so the initial
+    charge density vanishes identically; thermal momenta are drawn
+    independently (Gaussian per component, spread u_th for electrons and
+    u_th (m_partner / m_e)^(1/2) for partners: equal temperatures), and their
+    current noise seeds the instability.  Densities follow the
+    paper's normalisation: the relativistic electron plasma frequency
+    (n_e / gamma)^(1/2) is 1 (n_e summed over both beams)."""
+    n: int = 64
+    d: float = 0.1
+    dt: float = 0.05
+    ppc: int = 4                # electron-partner pairs per cell and beam
+    gamma: float = 3.0
+    u_th: float = 0.01          # Gaussian thermal spread of each momentum component
+    mass_ratio: float = 64.0    # partner mass (1: pair plasma)
+    axis: int = 0               # streaming axis (0 = x, out of the simulation plane)
+    seed: int = 11
+
+    @property
+    def L(self) -> float:
+        return self.n * self.d
+
+    @property
+    def n_particles(self) -> int:
+        return 2 * 2 * self.ppc * self.n * self.n
+
+    def particles(self):
+        """x, u [3][N] and per-particle charge, mass, macro weight [N].  Order:
+        electrons of beam +, electrons of beam -, partners of beam +, partners
+        of beam - (partner i starts on electron i)."""
+        ne_beam = self.ppc * self.n * self.n
+        ne = 2 * ne_beam
+        L = self.L
+        x = np.stack([uniforms(self.seed, c, ne) * L for c in range(3)])
+        ue = np.stack([self.u_th * _stream(self.seed, 3 + c).standard_normal(ne) for c in range(3)])
+        up = np.stack([self.u_th * math.sqrt(self.mass_ratio) *
+                       _stream(self.seed, 6 + c).standard_normal(ne) for c in range(3)])
+        gb = float(self.gamma)
+        u0 = math.sqrt(gb * gb - 1.0)
+        for u in (ue, up):
+            u[self.axis, :ne_beam] += u0
+            u[self.axis, ne_beam:] -= u0
+        n_e = gb                                   # (n_e / gamma)^(1/2) = 1
+        w = n_e * self.d * self.d / (2 * self.ppc)  # electrons per cell: 2 ppc
+        X = np.concatenate([x, x], 1)
+        U = np.concatenate([ue, up], 1)
+        q = np.concatenate([-np.ones(ne), np.ones(ne)])
+        m = np.concatenate([np.ones(ne), self.mass_ratio * np.ones(ne)])
+        return X, U, q, m, np.full(2 * ne, w)
