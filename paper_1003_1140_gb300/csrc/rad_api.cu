@@ -789,6 +789,10 @@ static int complete_windows(rad_ctx* c, F copy)
     return RAD_OK;
 }
 
+namespace rad {
+cudaStream_t ctx_stream(const rad_ctx* c) { return c ? c->stream : nullptr; }
+}  // namespace rad
+
 extern "C" {
 
 int rad_init(rad_ctx** out, const double* dirs, int32_t D, const double* freqs,

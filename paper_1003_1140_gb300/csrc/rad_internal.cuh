@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+struct rad_ctx;   // the radiation context (rad_api.cu)
+
 namespace rad {
 
 // ---------------------------------------------------------------------------
@@ -268,6 +270,10 @@ struct Accum64Params {
 
 cudaError_t launch_ingest(const IngestParams& p, cudaStream_t st);
 const void* ingest_kernel_ptr();
+
+// Stream a radiation context orders its work on (for in-library callers that
+// hand it device buffers from another stream).
+cudaStream_t ctx_stream(const rad_ctx* c);
 // FP32 kernel variant: frequencies per thread, of which np by the FMA-pipe
 // polynomial, anchor interval K, coherent sum, minimum resident blocks per SM.
 struct Accum32Config {

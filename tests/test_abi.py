@@ -1,5 +1,6 @@
 """The C-ABI library builds for sm_103a, loads, and exports every entry point
-include/rad.h declares (no compute calls: this runs without a GPU)."""
+include/rad.h, rad_mlp.h and rad_pic.h declare (no compute calls: this runs
+without a GPU)."""
 import ctypes
 import os
 import re
@@ -24,7 +25,7 @@ def test_library_builds_loads_and_exports_everything():
     from paper_1003_1140_gb300 import build
     path = build.build()
     lib = ctypes.CDLL(path)
-    for header in ("rad.h", "rad_mlp.h"):
+    for header in ("rad.h", "rad_mlp.h", "rad_pic.h"):
         for name in declared_symbols(header):
             assert hasattr(lib, name), name
 
@@ -32,6 +33,11 @@ def test_library_builds_loads_and_exports_everything():
 def test_mlp_header_declares_the_binding_names():
     from paper_1003_1140_gb300 import mlp
     assert sorted(mlp.EXPORTED) == declared_symbols("rad_mlp.h")
+
+
+def test_pic_header_declares_the_binding_names():
+    from paper_1003_1140_gb300 import pic
+    assert sorted(pic.EXPORTED) == declared_symbols("rad_pic.h")
 
 
 def test_null_context_calls_fail_cleanly():
