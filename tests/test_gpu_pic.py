@@ -168,3 +168,17 @@ def test_pic_rejects_bad_arguments():
             p.tracked(0, 4, np.empty((3, 4)), np.empty((3, 4)))   # host buffers
     with pytest.raises(RuntimeError):
         pic.Pic(16, 0.1, 0.1, [(1, -1.0, 1.0, 1.0)], np.zeros((3, 1)), np.zeros((3, 1)))  # Courant
+
+
+def test_insitu_run_small():
+    """The in-situ application end to end on a small box: timings, growing
+    magnetic energy, finite positive spectra with a peak per window and observer."""
+    from paper_1003_1140_gb300 import insitu
+    res, spectra = insitu.run(n=32, ppc=2, steps=120, tracked=512, windows=2, n_omega=64,
+                              pic_only_steps=20, chunk=40)
+    assert res["pic_ms_per_step"] > 0 and res["coupled_ms_per_step"] > 0
+    assert res["diagnostic_updates"] == 512 * 120 * 6 * 64
+    assert res["magnetic_energy"][-1][1] > res["magnetic_energy"][0][1]
+    assert len(res["peak_omega"]) == 2 and len(res["peak_omega"][0]) == 6
+    for S in spectra:
+        assert np.isfinite(S).all() and (S >= 0).all() and S.max() > 0

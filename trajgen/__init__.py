@@ -342,10 +342,9 @@ class TwoStream:
 
     def particles(self):
         """x, u [3][N] and per-particle charge, mass, macro weight [N].  Order:
-        electrons of beam +, electrons of beam -, partners of beam +, partners
-        of beam - (partner i starts on electron i)."""
-        ne_beam = self.ppc * self.n * self.n
-        ne = 2 * ne_beam
+        the 2 ppc n^2 electrons (even index: beam +, odd: beam -), then their
+        partners in the same order (partner i starts on electron i)."""
+        ne = 2 * self.ppc * self.n * self.n
         L = self.L
         x = np.stack([uniforms(self.seed, c, ne) * L for c in range(3)])
         ue = np.stack([self.u_th * _stream(self.seed, 3 + c).standard_normal(ne) for c in range(3)])
@@ -353,9 +352,9 @@ class TwoStream:
                        _stream(self.seed, 6 + c).standard_normal(ne) for c in range(3)])
         gb = float(self.gamma)
         u0 = math.sqrt(gb * gb - 1.0)
+        sign = np.where(np.arange(ne) % 2 == 0, 1.0, -1.0)   # beams alternate by index
         for u in (ue, up):
-            u[self.axis, :ne_beam] += u0
-            u[self.axis, ne_beam:] -= u0
+            u[self.axis] += sign * u0
         n_e = gb                                   # (n_e / gamma)^(1/2) = 1
         w = n_e * self.d * self.d / (2 * self.ppc)  # electrons per cell: 2 ppc
         X = np.concatenate([x, x], 1)
