@@ -1,6 +1,6 @@
 // rad_accum32_ft8_mix.cu -- instantiations of the FP32 split-phase kernel
 // for the (frequencies per thread, polynomial frequencies, blocks per SM)
-// families (8,2,2), (8,2,3) and (8,1,2); see rad_accum32.cuh.
+// families (8,2,2), (8,2,3), (8,1,2) and (8,1,3); see rad_accum32.cuh.
 #include "rad_accum32.cuh"
 
 namespace rad {
@@ -18,6 +18,7 @@ bool accum32_ft8_mix(const Accum32Params* p, const Accum32Config& cfg, int grid,
     RAD_ACCUM32_FAMILY(8,2,2)
     RAD_ACCUM32_FAMILY(8,2,3)
     RAD_ACCUM32_FAMILY(8,1,2)
+    RAD_ACCUM32_FAMILY(8,1,3)
     return false;
 }
 

@@ -364,7 +364,7 @@ static int autotune32(rad_ctx* c, int K)
     }
     const bool coh = c->mode == RAD_COHERENT;
     std::vector<Accum32Config> cands = {{8, 0, K, coh, 2}, {8, 0, K, coh, 3}, {8, 1, K, coh, 2},
-                                        {8, 2, K, coh, 2}};
+                                        {8, 1, K, coh, 3}, {8, 2, K, coh, 2}};
     // small problems: not worth timing
     if (rad_updates(c) < (int64_t)2e10) {
         c->cfg = cands[0];

@@ -288,7 +288,22 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--out", default=None)
     ap.add_argument("--gemm-bench", action="store_true")
+    ap.add_argument("--train-steps", type=int, default=0,
+                    help="only run this many training steps of the workload's network on "
+                         "random device data (profiling)")
     a = ap.parse_args(argv)
+    if a.train_steps:
+        from . import mlp as M
+        net = M.MLP([768, 512, 512, 512, 393216], 128)
+        net.init_params(0)
+        x = torch.randn((128, 768), device="cuda")
+        t = torch.randn((128, 393216), device="cuda")
+        for _ in range(a.train_steps):
+            net.train_step(x, t, 1e-4)
+        torch.cuda.synchronize()
+        M.check()
+        net.close()
+        return None
     if a.gemm_bench:
         import json
         line = json.dumps(gemm_bench())
