@@ -40,8 +40,8 @@ METRIC = "G particle·step·ω·n updates/s, FP32 split vs FP64 GPU at ≤1e-4 r
 # in profiles/accum32_workload2_4096p.md (4096 particles, this workload's samples,
 # directions and omegas), valid while the kernel source and its work-list builder are
 # the ones that were captured; traffic scales with the particle count.
-TRAFFIC_CAPTURE = {"sources_sha256": "8ba0078ed1d86ae391c2aca0a57103234a3ea3481c0a2e379ac171de74d7d9b0",
-                   "bytes_per_launch": 776.647424e6, "particles": 4096}
+TRAFFIC_CAPTURE = {"sources_sha256": "5365a092915ef071bce500b57e2fa51314c31a378ccf018066fe1f1686301c50",
+                   "bytes_per_launch": 777.483264e6, "particles": 4096}
 UNIT = "G updates/s"
 WORKLOAD = 2
 
@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--anchor-K", type=int, default=None)
     ap.add_argument("--freq-per-lane", type=int, default=None)
     ap.add_argument("--blocks-per-sm", type=int, default=None)
+    ap.add_argument("--poly-per-lane", type=int, default=None)
     return ap.parse_args()
 
 
@@ -235,6 +236,8 @@ def main():
         opts["freq_per_lane"] = args.freq_per_lane
     if args.blocks_per_sm is not None:
         opts["blocks_per_sm"] = args.blocks_per_sm
+    if args.poly_per_lane is not None:
+        opts["poly_per_lane"] = args.poly_per_lane
     ctx = R.Radiation(w.dirs, w.grids, w.dt, sp, w.windows, precision=R.RAD_FP32_SPLIT,
                       box_L=w.L, options=opts or None)
     out = torch.empty(ctx.spectrum_size(), dtype=torch.float64, device="cuda")

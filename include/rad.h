@@ -121,7 +121,11 @@ typedef struct {
                               u linear in time between the half-step states,
                               betadot its exact derivative, r by Simpson's rule;
                               updates and the ring grow n-fold               */
-    int32_t reserved[8];
+    int32_t reserved[8];   /* [0]: 1 = time the ingest launches (rad_timing);
+                              [1]: MIX variant, frequencies of each thread on the
+                              FMA-pipe polynomial (0: 2 of 8, 4 of 16); after the
+                              first step rad_get_options reports the kernel build
+                              in use here (0 for SFU); others must be 0     */
 } rad_options;
 
 /*

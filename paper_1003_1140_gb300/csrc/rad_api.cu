@@ -1046,6 +1046,7 @@ int rad_get_options(const rad_ctx* c, rad_options* o)
         o->freq_per_lane = c->cfg.ft;
         o->blocks_per_sm = c->cfg.mb;
         o->variant = c->cfg.np > 0 ? RAD_VARIANT_MIX : RAD_VARIANT_SFU;
+        o->reserved[1] = c->cfg.np;
     }
     return RAD_OK;
 }

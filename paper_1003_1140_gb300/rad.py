@@ -237,7 +237,9 @@ class Radiation:
     def options(self) -> dict:
         o = rad_options()
         self._check(self._lib.rad_get_options(self._h, ctypes.byref(o)))
-        return {f: getattr(o, f) for f, _ in rad_options._fields_ if f != "reserved"}
+        out = {f: getattr(o, f) for f, _ in rad_options._fields_ if f != "reserved"}
+        out["poly_per_lane"] = int(o.reserved[1])
+        return out
 
     def accumulate(self, step, x, u):
         self._check(self._lib.rad_accumulate(self._h, int(step), _ptr(x), _ptr(u)))
