@@ -6,6 +6,7 @@
 // arithmetic step of the diagnostic runs in the kernels of rad_ingest.cu,
 // rad_accum32.cu, rad_accum64.cu and the finalize kernel below.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -100,6 +101,12 @@ struct rad_ctx {
     cudaEvent_t copy_done[2] = {nullptr, nullptr};
     cudaEvent_t used_done[2] = {nullptr, nullptr};
     int stage_next = 0;
+    // blocked host path: per-block staging, per-(event, block) work lists
+    double* bstage[2] = {nullptr, nullptr};
+    size_t bstage_bytes = 0;
+    int blk_count = 0;                               // blocks the lists were built for
+    std::vector<std::vector<Event>> blk_events;      // [event][block]
+
 
     // events of the step axis
     std::vector<Event> events;     // eager: sorted by call; defer: one event
@@ -206,7 +213,10 @@ static int freq_tile(const rad_ctx* c)
 }
 
 // Build the work items of one event (set of windows) and sort by cost.
-static void build_items(rad_ctx* c, Event& ev, int total_blocks)
+// Work items of an event's windows; with [tlo, thi) only the particle tiles in
+// that range (the blocked host path; single species), the groups sized for the
+// range so that every list balances over the GPU.
+static void build_items(rad_ctx* c, Event& ev, int total_blocks, int tlo = 0, int thi = INT_MAX)
 {
     const int ftl = freq_tile(c);
     const int ch = chunk_len(c);
@@ -216,8 +226,11 @@ static void build_items(rad_ctx* c, Event& ev, int total_blocks)
         const rad_window& W = c->wins[w];
         const int nft = (c->grid_len[W.freq_grid] + ftl - 1) / ftl;
         for (int s = 0; s < c->n_species; ++s)
-            if ((W.species_mask >> s) & 1u)
-                units += (double)((c->species[s].count + kTileP - 1) / kTileP) * nft * c->D;
+            if ((W.species_mask >> s) & 1u) {
+                const int nts = (int)((c->species[s].count + kTileP - 1) / kTileP);
+                const int in_range = std::max(0, std::min(nts, thi) - std::max(0, tlo));
+                units += (double)in_range * nft * c->D;
+            }
     }
     const double target_items = 64.0 * std::max(1, total_blocks);
     int G = (int)std::max(1.0, std::floor(units / target_items));
@@ -231,13 +244,14 @@ static void build_items(rad_ctx* c, Event& ev, int total_blocks)
         for (int s = 0; s < c->n_species; ++s) {
             if (!((W.species_mask >> s) & 1u) || c->species[s].count == 0) continue;
             const int nt = (int)((c->species[s].count + kTileP - 1) / kTileP);
+            const int t_end = std::min(nt, thi);
             // tile-group-major: the items that read the same particles
             // (all directions and frequency tiles) are adjacent in the list,
             // so they run at about the same time and share L2
-            for (int t0 = 0; t0 < nt; t0 += G)
+            for (int t0 = std::max(0, tlo); t0 < t_end; t0 += G)
                 for (int d = 0; d < c->D; ++d)
                     for (int f = 0; f < nft; ++f) {
-                        WorkItem it{w, d, f, s, t0, std::min(G, nt - t0)};
+                        WorkItem it{w, d, f, s, t0, std::min(G, t_end - t0)};
                         ev.items.push_back(it);
                         cost.push_back((int64_t)it.ntiles * nch);
                     }
@@ -583,8 +597,9 @@ static int launch_event(rad_ctx* c, Event& ev)
     return RAD_OK;
 }
 
-// Ingest n steps from device arrays x, u ([n][3][n_in]) starting at step0.
-static int ingest_device(rad_ctx* c, int64_t step0, int64_t n, const double* x, const double* u)
+// The context's part of an ingest launch (inputs, step range and particle
+// range are the caller's).
+static IngestParams ingest_params(const rad_ctx* c)
 {
     IngestParams p{};
     p.n_in = c->n_in;
@@ -608,6 +623,13 @@ static int ingest_device(rad_ctx* c, int64_t step0, int64_t n, const double* x, 
     p.sel = c->d_sel;
     p.n_sel = c->n_sel;
     p.nsub = c->nsub;
+    return p;
+}
+
+// Ingest n steps from device arrays x, u ([n][3][n_in]) starting at step0.
+static int ingest_device(rad_ctx* c, int64_t step0, int64_t n, const double* x, const double* u)
+{
+    IngestParams p = ingest_params(c);
     int64_t s = step0;
     const int64_t end = step0 + n;
     while (s < end) {
@@ -639,6 +661,153 @@ static int ingest_device(rad_ctx* c, int64_t step0, int64_t n, const double* x, 
         }
         s = stop;
     }
+    return RAD_OK;
+}
+
+// Host inputs, one species, eager windows: the particle axis is cut into a few
+// blocks of whole tiles.  Each block's share of the call's steps is copied
+// (pitched copies on the copy stream, double-buffered) and ingested on its own,
+// and at every window close only that block's work items are launched.  The
+// copies of block b + 1 run while block b is ingested and accumulated, so the
+// transfer hides behind the accumulation instead of preceding it.  Per-particle
+// ingest state makes the blocks independent; each block's ring columns are
+// read by its own accumulation before its next segment is ingested.  Blocks
+// grow geometrically (1/32 of the tiles, then x4): only the first, small
+// block's transfer is exposed, and each later transfer (4x the previous block's
+// particles, at ~1/8 of its accumulation time per particle) fits behind it.
+constexpr int kHostBlocks = 4;      // gates the path: n_in >= 64 tiles per block
+// per staging buffer: a whole block of a long call fits (the largest block of
+// 65,536 particles x 4097 calls: 6.4 GB), so block b + 1 is copied entirely while block b is
+// accumulated; longer segments arrive in chunks, whose last copy waits for the
+// block's first ingest
+constexpr size_t kBlockStageBytes = size_t(8) << 30;
+
+// Tile boundaries of the blocks: 1/32 of the tiles, then each block 4x the
+// previous one, the remainder merged into the last block when it is small.
+static std::vector<int> block_bounds(int nt)
+{
+    std::vector<int> b = {0};
+    int cur = std::max(1, nt / 32);
+    while (b.back() < nt) {
+        int next = std::min(nt, b.back() + cur);
+        if (nt - next < cur / 2) next = nt;
+        b.push_back(next);
+        cur *= 4;
+    }
+    return b;
+}
+
+static int blocked_lists(rad_ctx* c, const std::vector<int>& bounds)
+{
+    const int nblocks = (int)bounds.size() - 1;
+    if (c->blk_count == nblocks) return RAD_OK;
+    for (auto& row : c->blk_events)
+        for (auto& ev : row) cudaFree(ev.d_items);
+    c->blk_events.assign(c->events.size(), std::vector<Event>(nblocks));
+    const int total_blocks = blocks_per_sm(c) * c->sms;
+    for (size_t e = 0; e < c->events.size(); ++e)
+        for (int b = 0; b < nblocks; ++b) {
+            Event& ev = c->blk_events[e][b];
+            ev.call = c->events[e].call;
+            ev.wins = c->events[e].wins;
+            build_items(c, ev, total_blocks, bounds[b], bounds[b + 1]);
+            if (!ev.items.empty()) {
+                CU(cudaMalloc(&ev.d_items, ev.items.size() * sizeof(WorkItem)));
+                CU(cudaMemcpy(ev.d_items, ev.items.data(), ev.items.size() * sizeof(WorkItem),
+                              cudaMemcpyHostToDevice));
+            }
+        }
+    c->blk_count = nblocks;
+    return RAD_OK;
+}
+
+// The blocked path (see above).  Ingest and accumulation stay in order on the
+// context's stream; only the copies run ahead on the copy stream.  (Ingesting
+// block b + 1 on a second stream during block b's accumulation, or blocking
+// device-resident inputs too, measured slower: the extra launch tails cost more
+// than the overlap saves.)
+static int ingest_host_blocked(rad_ctx* c, int64_t step0, int64_t n, const double* x,
+                               const double* u)
+{
+    const int64_t N = c->n_in;
+    const int nt = (int)((N + kTileP - 1) / kTileP);
+    const std::vector<int> bounds = block_bounds(nt);
+    const int nblocks = (int)bounds.size() - 1;
+    int64_t ppb = 0;                                                  // largest block
+    for (int b = 0; b < nblocks; ++b)
+        ppb = std::max<int64_t>(ppb, (int64_t)(bounds[b + 1] - bounds[b]) * kTileP);
+    int rc = blocked_lists(c, bounds);
+    if (rc) return rc;
+    const size_t cap = c->opt.reserved[2] > 0 ? (size_t)c->opt.reserved[2] << 20 : kBlockStageBytes;
+    const int64_t chunk = std::max<int64_t>(1, (int64_t)(cap / (6 * ppb * sizeof(double))));
+    const size_t need = (size_t)std::min<int64_t>(chunk, n) * 6 * ppb * sizeof(double);
+    if (c->bstage_bytes < need) {
+        CU(cudaStreamSynchronize(c->stream));
+        CU(cudaStreamSynchronize(c->copy_stream));
+        for (int b = 0; b < 2; ++b) {
+            if (c->bstage[b]) CU(cudaFree(c->bstage[b]));
+            c->bstage[b] = nullptr;
+        }
+        c->bstage_bytes = 0;
+        for (int b = 0; b < 2; ++b) CU(cudaMalloc(&c->bstage[b], need));
+        c->bstage_bytes = need;
+    }
+    IngestParams p = ingest_params(c);
+    const int64_t end = step0 + n;
+    int64_t s = step0;
+    while (s < end) {
+        // segment: up to and including the next closing call
+        int64_t stop = end;
+        auto itv = c->event_at.lower_bound(s);
+        if (itv != c->event_at.end() && itv->first < end) stop = itv->first + 1;
+        const int ev_idx = (itv != c->event_at.end() && itv->first == stop - 1) ? itv->second : -1;
+        for (int b = 0; b < nblocks; ++b) {
+            const int64_t p0 = (int64_t)bounds[b] * kTileP;
+            const int64_t pc = std::min<int64_t>((int64_t)bounds[b + 1] * kTileP, N) - p0;
+            for (int64_t t = s; t < stop; t += chunk) {
+                const int64_t m = std::min(chunk, stop - t);
+                const int buf = c->stage_next;
+                c->stage_next ^= 1;
+                double* sx = c->bstage[buf];
+                double* su = sx + m * 3 * pc;
+                CU(cudaStreamWaitEvent(c->copy_stream, c->used_done[buf], 0));
+                const double* xs = x + ((t - step0) * 3) * N + p0;
+                const double* us = u + ((t - step0) * 3) * N + p0;
+                CU(cudaMemcpy2DAsync(sx, pc * sizeof(double), xs, N * sizeof(double),
+                                     pc * sizeof(double), (size_t)(m * 3), cudaMemcpyHostToDevice,
+                                     c->copy_stream));
+                CU(cudaMemcpy2DAsync(su, pc * sizeof(double), us, N * sizeof(double),
+                                     pc * sizeof(double), (size_t)(m * 3), cudaMemcpyHostToDevice,
+                                     c->copy_stream));
+                CU(cudaEventRecord(c->copy_done[buf], c->copy_stream));
+                CU(cudaStreamWaitEvent(c->stream, c->copy_done[buf], 0));
+                p.x = sx;
+                p.u = su;
+                p.step0 = t;
+                p.n_steps = (int32_t)m;
+                p.first = p0;
+                p.count = pc;
+                p.ld = pc;
+                p.xoff = p0;
+                if (c->time_ingest)
+                    CU(cudaEventRecord(next_event(c->ing_ev, c->ing_used, true), c->stream));
+                cudaError_t e = launch_ingest(p, c->stream);
+                if (e != cudaSuccess)
+                    return fail(c, RAD_ECUDA, "ingest launch failed: %s", cudaGetErrorString(e));
+                if (c->time_ingest)
+                    CU(cudaEventRecord(next_event(c->ing_ev, c->ing_used, false), c->stream));
+                ++c->ing_launches;
+                CU(cudaEventRecord(c->used_done[buf], c->stream));
+            }
+            if (ev_idx >= 0) {
+                rc = launch_event(c, c->blk_events[ev_idx][b]);
+                if (rc) return rc;
+            }
+        }
+        s = stop;
+    }
+    // the caller may reuse its host buffers once this returns
+    CU(cudaStreamSynchronize(c->copy_stream));
     return RAD_OK;
 }
 
@@ -707,32 +876,11 @@ static int graph_for(rad_ctx* c, int kind, const IngestParams& ip, StepGraph** o
 // One step through its graph: patch the ingest node's parameters, replay.
 static int step_via_graph(rad_ctx* c, int64_t step, const double* x, const double* u)
 {
-    IngestParams p{};
+    IngestParams p = ingest_params(c);
     p.x = x;
     p.u = u;
-    p.n_in = c->n_in;
     p.n_steps = 1;
     p.step0 = step;
-    p.dt = c->dt;
-    p.box_L = c->box_L;
-    p.x_prev = c->x_prev;
-    p.r_prev = c->r_prev;
-    p.u_prev = c->u_prev;
-    p.slab32 = c->slab32;
-    p.slab64 = c->slab64;
-    p.anc32 = c->anc32;
-    p.ncols = c->ncols;
-    p.ring = c->ring;
-    p.K = c->K;
-    p.nblk = c->nblk;
-    p.n_species = c->n_species;
-    for (int s = 0; s <= c->n_species; ++s) p.in_off[s] = c->in_off[s];
-    for (int s = 0; s < c->n_species; ++s) p.col_off[s] = c->col_off[s];
-    p.check = c->opt.check_inputs;
-    p.err_word = c->d_err;
-    p.sel = c->d_sel;
-    p.n_sel = c->n_sel;
-    p.nsub = c->nsub;
     int kind = 0;
     if (!c->opt.defer) {
         auto itv = c->event_at.find(step);
@@ -1069,6 +1217,10 @@ int rad_accumulate_steps(rad_ctx* c, int64_t step0, int64_t n, const double* x, 
     } else if (dx && du) {
         rc = ingest_device(c, step0, n, x, u);
         if (rc) return rc;
+    } else if (!dx && !du && c->n_species == 1 && !c->opt.defer && n >= 64 &&
+               c->n_in >= 64 * kTileP * kHostBlocks) {
+        rc = ingest_host_blocked(c, step0, n, x, u);
+        if (rc) return rc;
     } else {
         // host inputs: double-buffered staging on a copy stream
         const int64_t per = 3 * c->n_in;
@@ -1209,10 +1361,12 @@ void rad_destroy(rad_ctx* c)
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto& ev : c->events) cudaFree(ev.d_items);
+    for (auto& row : c->blk_events)
+        for (auto& ev : row) cudaFree(ev.d_items);
     void* bufs[] = {c->slab32, c->slab64, c->anc32, c->x_prev, c->r_prev, c->u_prev,
                     c->d_dirs32, c->d_dirs64, c->d_om32, c->d_nuhi, c->d_nulo,
                     c->d_om64, c->d_wins, c->d_sel, c->d_species, c->acc, c->d_out, c->d_err, c->d_counter,
-                    c->stage[0], c->stage[1]};
+                    c->stage[0], c->stage[1], c->bstage[0], c->bstage[1]};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (auto& pr : c->acc_ev) {

@@ -51,8 +51,11 @@ __device__ uint32_t selector_bits(const IngestParams& p, const double x[3], cons
 
 __global__ void __launch_bounds__(256) ingest_kernel(const IngestParams p)
 {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= p.n_in) return;
+    const int64_t i = p.first + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t cnt = p.count ? p.count : p.n_in - p.first;
+    if (i >= p.first + cnt) return;
+    const int64_t ld = p.ld ? p.ld : p.n_in;    // input particle stride
+    const int64_t xi = i - p.xoff;              // input column of particle i
     int sp = 0;
     while (sp + 1 < p.n_species && i >= p.in_off[sp + 1]) ++sp;
     const int64_t col = p.col_off[sp] + (i - p.in_off[sp]);
@@ -81,8 +84,8 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestParams p)
     // the next step's inputs are loaded while this step is being processed
     double xq[3], uq[3];
     for (int c = 0; c < 3; ++c) {
-        xq[c] = p.n_steps > 0 ? p.x[c * p.n_in + i] : 0.0;
-        uq[c] = p.n_steps > 0 ? p.u[c * p.n_in + i] : 0.0;
+        xq[c] = p.n_steps > 0 ? p.x[c * ld + xi] : 0.0;
+        uq[c] = p.n_steps > 0 ? p.u[c * ld + xi] : 0.0;
     }
     for (int t = 0; t < p.n_steps; ++t) {
         const int64_t s = p.step0 + t;
@@ -92,11 +95,11 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestParams p)
             un[c] = uq[c];
         }
         if (t + 1 < p.n_steps) {
-            const double* xs = p.x + (int64_t)(t + 1) * 3 * p.n_in;
-            const double* us = p.u + (int64_t)(t + 1) * 3 * p.n_in;
+            const double* xs = p.x + (int64_t)(t + 1) * 3 * ld;
+            const double* us = p.u + (int64_t)(t + 1) * 3 * ld;
             for (int c = 0; c < 3; ++c) {
-                xq[c] = xs[c * p.n_in + i];
-                uq[c] = us[c * p.n_in + i];
+                xq[c] = xs[c * ld + xi];
+                uq[c] = us[c * ld + xi];
             }
         }
         if (p.check) {
@@ -289,9 +292,14 @@ const void* ingest_kernel_ptr() { return reinterpret_cast<const void*>(&ingest_k
 
 cudaError_t launch_ingest(const IngestParams& p, cudaStream_t st)
 {
-    if (p.n_in == 0 || p.n_steps == 0) return cudaSuccess;
-    const int threads = 256;
-    const int64_t blocks = (p.n_in + threads - 1) / threads;
+    const int64_t cnt = p.count ? p.count : p.n_in - p.first;
+    if (cnt <= 0 || p.n_steps == 0) return cudaSuccess;
+    // one thread per particle, small blocks: the kernel is bound by its FP64
+    // work per SM, so the blocks must spread evenly over all 152 SMs (256-thread
+    // blocks left 65,536 particles at two blocks on most SMs and one on the rest,
+    // and a 16,384-particle share on 64 SMs)
+    const int threads = 64;
+    const int64_t blocks = (cnt + threads - 1) / threads;
     ingest_kernel<<<(unsigned)blocks, threads, 0, st>>>(p);
     return cudaGetLastError();
 }

@@ -233,6 +233,14 @@ struct IngestParams {
     const SelectorDev* sel; // selectors (device) or nullptr
     int32_t n_sel;
     int32_t nsub;           // sub-samples per PIC sample (<= 1: none)
+    // particle range of this launch and layout of x/u (zero: all particles,
+    // x/u holding every particle): particles first .. first + count - 1 are
+    // processed; particle i is column i - xoff of x/u, whose particle axis
+    // has stride ld
+    int64_t first;
+    int64_t count;
+    int64_t ld;
+    int64_t xoff;
 };
 
 struct Accum32Params {

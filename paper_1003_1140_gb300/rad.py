@@ -210,6 +210,8 @@ class Radiation:
                 o.reserved[0] = int(v)
             elif k == "poly_per_lane":
                 o.reserved[1] = int(v)
+            elif k == "host_stage_mib":
+                o.reserved[2] = int(v)
             else:
                 setattr(o, k, int(v))
         self._check(self._lib.rad_set_options(self._h, ctypes.byref(o)))

@@ -358,3 +358,30 @@ def test_subcycling_matches_oracle(two_species, precision, coherent):
         r.accumulate_steps(0, torch.as_tensor(X, device="cuda"), torch.as_tensor(U, device="cuda"))
         got = r.finalize()
     _check(got, ref, 1e-10 if precision == 0 else 1e-4, per_direction=True)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("coherent", [False, True])
+def test_host_blocked_transfer(precision, coherent):
+    """Host inputs of one species over 2050 particles: the particle-blocked
+    transfer (blocks of 8, 32, 128 and 89 tiles; windows closing at three calls
+    inside the batch; a 1 MiB staging cap so a block's segment arrives in
+    several chunks) gives the device-input and the deferred single-launch
+    results (FP64 summation order aside) and the oracle's."""
+    R = _rad()
+    w = trajgen.Workload("blocked", [(2050, -1.0, 1.0, 3.0)], 181, 0.05,
+                         np.array([[0.0, 1.0, 0.0], [1.0, 0.0, 0.0], [0.6, 0.0, 0.8]]),
+                         [trajgen.log_grid(0.1, 200.0, 64)],
+                         [(0, 180, 1, 0), (30, 120, 1, 0), (100, 100, 1, 0), (60, 90, 1, 0)],
+                         b_rms=0.3)
+    X, U = w.trajectory_numpy()
+    dev = _run(w, X, U, precision, coherent)           # device inputs: one launch
+    host = _run(w, X, U, precision, coherent, options={"host_stage_mib": 1}, device_inputs=False)
+    whole = _run(w, X, U, precision, coherent, options={"defer": 1})   # one launch, all particles
+    for g, e in zip(host, whole):
+        np.testing.assert_allclose(g, e, rtol=1e-11, atol=1e-300)
+    for g, e in zip(dev, whole):
+        np.testing.assert_allclose(g, e, rtol=1e-11, atol=1e-300)
+    ref = oracle.spectra(X, U, w.dt, w.dirs, w.grids, w.windows, [(2050, -1.0)],
+                         coherent=coherent, box_L=w.L)
+    _check(host, ref, 1e-10 if precision == R.RAD_FP64 else 1e-4, per_direction=True)
