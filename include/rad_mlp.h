@@ -60,6 +60,18 @@ int rad_mlp_forward(rad_mlp *m, int32_t batch, const float *x, float *y);
  * layer (read them with rad_mlp_get_layer); *loss (host, may be NULL) gets the MSE. */
 int rad_mlp_gradients(rad_mlp *m, int32_t batch, const float *x, const float *t, double *loss);
 
+/* The surrogate's data transforms, for rad_mlp_predict: per input feature
+ * x' = (log10(max(x, floor_value)) - in_mu) / in_sd, per output feature
+ * y = 10^(z out_sd + out_mu) ([w_0] and [w_L] FP32 values each, host or
+ * device; floor_value > 0).  The statistics are the training set's. */
+int rad_mlp_set_transform(rad_mlp *m, const float *in_mu, const float *in_sd, const float *out_mu,
+                          const float *out_sd, float floor_value);
+
+/* Prediction in physical units: the input transform, the forward pass and the
+ * output transform, all on the device; x [batch][w_0] raw inputs, y
+ * [batch][w_L] (host or device).  RAD_MLP_EINVAL before rad_mlp_set_transform. */
+int rad_mlp_predict(rad_mlp *m, int32_t batch, const float *x, float *y);
+
 /* One Adam step from the stored gradients (bias-corrected; FP32 master weights,
  * BF16 copies of W and W^T refreshed).  Stream ordered; does not wait. */
 int rad_mlp_adam(rad_mlp *m, float lr, float beta1, float beta2, float eps);

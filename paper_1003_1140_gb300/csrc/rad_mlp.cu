@@ -479,6 +479,35 @@ __global__ void to_bf16_rows(const float* x, bf16* y, int rows_valid, int rows, 
     }
 }
 
+// Input transform of rad_mlp_predict: h0 = BF16((log10(max(x, floor)) - mu) / sd)
+// per feature (padded rows zero).
+__global__ void log_standardise_rows(const float* __restrict__ x, bf16* __restrict__ y,
+                                     const float* __restrict__ mu, const float* __restrict__ sd,
+                                     float floor_v, int rows_valid, int rows, int cols)
+{
+    const int64_t n = (int64_t)rows * cols;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(i / cols), c = (int)(i - (int64_t)r * cols);
+        float v = 0.0f;
+        if (r < rows_valid) v = (log10f(fmaxf(x[i], floor_v)) - mu[c]) / sd[c];
+        y[i] = __float2bfloat16_rn(v);
+    }
+}
+
+// Output transform of rad_mlp_predict: y = 10^(z sd + mu) per feature.
+__global__ void exp10_affine_rows(const float* __restrict__ z, float* __restrict__ y,
+                                  const float* __restrict__ mu, const float* __restrict__ sd,
+                                  int rows_valid, int cols)
+{
+    const int64_t n = (int64_t)rows_valid * cols;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % cols);
+        y[i] = exp10f(fmaf(z[i], sd[c], mu[c]));
+    }
+}
+
 // MSE over the valid rows, loss = sum (y - t)^2 / (rows_valid * cols), and its
 // gradient g = 2 (y - t) / (rows_valid * cols) (FP32 and BF16; zero on padded rows).
 // In 32 x 32 tiles, also writing BF16 G^T [cols][rows]
@@ -668,6 +697,12 @@ struct rad_mlp {
     double* loss_part = nullptr;    // per-block loss shares of mse_tile
     float* xin = nullptr;           // staging for host inputs [rows][w[0]]
     float* work = nullptr;          // split-K partial sums (largest split product)
+    float* in_mu = nullptr;         // rad_mlp_predict transforms [w[0]], [w[L]] (null: unset)
+    float* in_sd = nullptr;
+    float* out_mu = nullptr;
+    float* out_sd = nullptr;
+    float floor_v = 0.0f;
+    float* ypred = nullptr;         // predict output staging [rows][w[L]]
     bf16* gt = nullptr;             // G^T [w][rows] for the weight gradient (largest layer)
     bf16* ht = nullptr;             // H^T [w][rows]
     int* err = nullptr;             // GEMM timeout word
@@ -796,7 +831,7 @@ int rad_mlp_get_layer(rad_mlp* m, int32_t layer, float* W, float* b, float* dW, 
     return RAD_MLP_OK;
 }
 
-static int forward(rad_mlp* m, int32_t batch, const float* x)
+static int forward(rad_mlp* m, int32_t batch, const float* x, bool transform = false)
 {
     const int R = round128(batch);
     const float* xd = x;
@@ -804,7 +839,11 @@ static int forward(rad_mlp* m, int32_t batch, const float* x)
         MCU(cudaMemcpyAsync(m->xin, x, (size_t)batch * m->w[0] * 4, cudaMemcpyHostToDevice, m->st));
         xd = m->xin;
     }
-    to_bf16_rows<<<grid_for((int64_t)R * m->w[0]), 256, 0, m->st>>>(xd, m->h[0], batch, R, m->w[0]);
+    if (transform)
+        log_standardise_rows<<<grid_for((int64_t)R * m->w[0]), 256, 0, m->st>>>(
+            xd, m->h[0], m->in_mu, m->in_sd, m->floor_v, batch, R, m->w[0]);
+    else
+        to_bf16_rows<<<grid_for((int64_t)R * m->w[0]), 256, 0, m->st>>>(xd, m->h[0], batch, R, m->w[0]);
     MCU(cudaGetLastError());
     for (int l = 0; l < m->L; ++l) {
         const bool last = l == m->L - 1;
@@ -822,6 +861,45 @@ int rad_mlp_forward(rad_mlp* m, int32_t batch, const float* x, float* y)
     int rc = forward(m, batch, x);
     if (rc) return rc;
     MCU(cudaMemcpyAsync(y, m->z[m->L], (size_t)batch * m->w[m->L] * 4, cudaMemcpyDefault, m->st));
+    MCU(cudaStreamSynchronize(m->st));
+    return gemm_timed_out() ? RAD_MLP_ETIMEOUT : RAD_MLP_OK;
+}
+
+int rad_mlp_set_transform(rad_mlp* m, const float* in_mu, const float* in_sd, const float* out_mu,
+                          const float* out_sd, float floor_value)
+{
+    if (!m || !in_mu || !in_sd || !out_mu || !out_sd || !(floor_value > 0.0f))
+        return fail(RAD_MLP_EINVAL, "rad_mlp_set_transform: null statistics or floor <= 0");
+    const int wi = m->w[0], wo = m->w[m->L];
+    if (!m->in_mu) {
+        MCU(cudaMalloc(&m->in_mu, (size_t)wi * 4));
+        MCU(cudaMalloc(&m->in_sd, (size_t)wi * 4));
+        MCU(cudaMalloc(&m->out_mu, (size_t)wo * 4));
+        MCU(cudaMalloc(&m->out_sd, (size_t)wo * 4));
+        MCU(cudaMalloc(&m->ypred, (size_t)m->max_rows * wo * 4));
+    }
+    MCU(cudaMemcpyAsync(m->in_mu, in_mu, (size_t)wi * 4, cudaMemcpyDefault, m->st));
+    MCU(cudaMemcpyAsync(m->in_sd, in_sd, (size_t)wi * 4, cudaMemcpyDefault, m->st));
+    MCU(cudaMemcpyAsync(m->out_mu, out_mu, (size_t)wo * 4, cudaMemcpyDefault, m->st));
+    MCU(cudaMemcpyAsync(m->out_sd, out_sd, (size_t)wo * 4, cudaMemcpyDefault, m->st));
+    MCU(cudaStreamSynchronize(m->st));
+    m->floor_v = floor_value;
+    return RAD_MLP_OK;
+}
+
+int rad_mlp_predict(rad_mlp* m, int32_t batch, const float* x, float* y)
+{
+    if (!m || batch < 1 || batch > m->max_rows || !x || !y) return RAD_MLP_EINVAL;
+    if (!m->in_mu) return fail(RAD_MLP_EINVAL, "rad_mlp_predict: no transform set");
+    int rc = forward(m, batch, x, true);
+    if (rc) return rc;
+    const int wo = m->w[m->L];
+    float* yd = is_dev(y) ? y : m->ypred;
+    exp10_affine_rows<<<grid_for((int64_t)batch * wo), 256, 0, m->st>>>(m->z[m->L], yd, m->out_mu,
+                                                                       m->out_sd, batch, wo);
+    MCU(cudaGetLastError());
+    if (yd != y)
+        MCU(cudaMemcpyAsync(y, yd, (size_t)batch * wo * 4, cudaMemcpyDeviceToHost, m->st));
     MCU(cudaStreamSynchronize(m->st));
     return gemm_timed_out() ? RAD_MLP_ETIMEOUT : RAD_MLP_OK;
 }
@@ -958,6 +1036,9 @@ void rad_mlp_destroy(rad_mlp* m)
     for (auto* vv : {&m->Wb, &m->Wbt, &m->h, &m->gb})
         for (bf16* p : *vv)
             if (p) cudaFree(p);
+    for (void* p : {(void*)m->in_mu, (void*)m->in_sd, (void*)m->out_mu, (void*)m->out_sd,
+                    (void*)m->ypred})
+        if (p) cudaFree(p);
     for (void* p : {(void*)m->t, (void*)m->g, (void*)m->loss, (void*)m->loss_part, (void*)m->xin,
                     (void*)m->work,
                     (void*)m->gt, (void*)m->ht})

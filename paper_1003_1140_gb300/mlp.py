@@ -10,6 +10,7 @@ from . import rad as _rad
 RAD_MLP_OK = 0
 EXPORTED = ("rad_mlp_init", "rad_mlp_set_layer", "rad_mlp_get_layer", "rad_mlp_forward",
             "rad_mlp_gradients", "rad_mlp_adam", "rad_mlp_gemm", "rad_mlp_check",
+            "rad_mlp_set_transform", "rad_mlp_predict",
             "rad_mlp_last_error", "rad_mlp_destroy")
 
 
@@ -34,6 +35,10 @@ def _lib():
                                      ctypes.c_float]
         lib.rad_mlp_gemm.restype = ctypes.c_int
         lib.rad_mlp_gemm.argtypes = [ctypes.c_int32] * 5 + [vp, vp, vp]
+        lib.rad_mlp_set_transform.restype = ctypes.c_int
+        lib.rad_mlp_set_transform.argtypes = [vp, vp, vp, vp, vp, ctypes.c_float]
+        lib.rad_mlp_predict.restype = ctypes.c_int
+        lib.rad_mlp_predict.argtypes = [vp, ctypes.c_int32, vp, vp]
         lib.rad_mlp_check.restype = ctypes.c_int
         lib.rad_mlp_check.argtypes = []
         lib.rad_mlp_last_error.restype = ctypes.c_char_p
@@ -101,6 +106,18 @@ class MLP:
         if y is None:
             y = np.empty((x.shape[0], self.widths[-1]), np.float32)
         self._chk(self._lib.rad_mlp_forward(self.h, x.shape[0], _p(x), _p(y)), "rad_mlp_forward")
+        return y
+
+    def set_transform(self, in_mu, in_sd, out_mu, out_sd, floor):
+        arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (in_mu, in_sd, out_mu, out_sd)]
+        self._chk(self._lib.rad_mlp_set_transform(self.h, *[_p(a) for a in arrs], float(floor)),
+                  "rad_mlp_set_transform")
+
+    def predict(self, x, y=None):
+        """Physical-unit prediction (transforms on the device)."""
+        if y is None:
+            y = np.empty((x.shape[0], self.widths[-1]), np.float32)
+        self._chk(self._lib.rad_mlp_predict(self.h, x.shape[0], _p(x), _p(y)), "rad_mlp_predict")
         return y
 
     def gradients(self, x, t):

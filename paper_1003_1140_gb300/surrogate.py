@@ -150,6 +150,16 @@ class Surrogate:
         self.batch = 128
         self.net = MLP([self.in_pad, *spec.hidden, self.out_pad], self.batch)
         self.net.init_params(seed)
+        # the same transforms on the device for prediction; padded input
+        # features (raw 0 -> log10 floor) map to 0 as in training
+        lf = math.log10(FLOOR)
+        in_mu = np.full(self.in_pad, lf)
+        in_sd = np.ones(self.in_pad)
+        in_mu[: self.in_dim], in_sd[: self.in_dim] = self.nx.mu, self.nx.sd
+        out_mu = np.zeros(self.out_pad)
+        out_sd = np.ones(self.out_pad)
+        out_mu[: self.out_dim], out_sd[: self.out_dim] = self.ny.mu, self.ny.sd
+        self.net.set_transform(in_mu, in_sd, out_mu, out_sd, FLOOR)
 
     def _x(self, sparse):
         x = np.zeros((len(sparse), self.in_pad), np.float32)
@@ -187,16 +197,17 @@ class Surrogate:
         return losses
 
     def predict(self, sparse):
+        """Dense spectra from raw sparse spectra: log/standardise, the network and
+        the inverse transform all run on the device (rad_mlp_predict)."""
         import torch
-        X = torch.as_tensor(self._x(sparse), device="cuda")
-        out = []
+        raw = np.zeros((len(sparse), self.in_pad), np.float32)
+        raw[:, : self.in_dim] = sparse.reshape(len(sparse), -1)
+        X = torch.as_tensor(raw, device="cuda")
+        Y = torch.empty((len(sparse), self.out_pad), dtype=torch.float32, device="cuda")
         for s in range(0, len(X), self.batch):
-            xb = X[s:s + self.batch].contiguous()
-            yb = torch.empty((len(xb), self.out_pad), dtype=torch.float32, device="cuda")
-            self.net.forward(xb, yb)
-            out.append(yb[:, : self.out_dim].cpu().numpy())
-        z = np.concatenate(out)
-        return self.ny.inverse(z).reshape((len(sparse),) + self.dense_shape)
+            self.net.predict(X[s:s + self.batch], Y[s:s + self.batch])
+        return Y[:, : self.out_dim].cpu().numpy().astype(np.float64).reshape(
+            (len(sparse),) + self.dense_shape)
 
 
 def interpolate_baseline(spec: SurrogateSpec, sparse):

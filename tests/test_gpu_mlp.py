@@ -1,5 +1,7 @@
 """The surrogate network's tensor-core kernels against the FP64 MLP reference,
 and a small end-to-end surrogate trained and judged on the GPU."""
+import math
+
 import numpy as np
 import pytest
 
@@ -105,6 +107,34 @@ def test_gradients_and_adam_match_reference():
         W, b = net.get_layer(l)
         w_exp, _, _ = ref.adam(Ws[l].astype(np.float64), 0.0, 0.0, grads[l][0].astype(np.float64), 1, 1e-2)
         assert np.abs(W - w_exp).max() <= 1e-5
+    net.close()
+
+
+def test_predict_applies_transforms_on_device():
+    """rad_mlp_predict = log10/standardise -> forward -> 10^(z sd + mu), against
+    the same three steps composed on the host around the raw forward pass."""
+    from paper_1003_1140_gb300 import mlp
+    rng = np.random.default_rng(8)
+    widths = [256, 128, 384]
+    net = mlp.MLP(widths, 64)
+    net.init_params(3)
+    x = (10.0 ** rng.uniform(-8, 2, size=(50, widths[0]))).astype(np.float32)
+    x[:, -6:] = 0.0                                       # padded features: raw zero
+    floor = 1e-30
+    in_mu = rng.normal(size=widths[0]) - 3.0
+    in_sd = rng.uniform(0.5, 2.0, size=widths[0])
+    in_mu[-6:], in_sd[-6:] = math.log10(floor), 1.0
+    out_mu = rng.normal(size=widths[-1])
+    out_sd = rng.uniform(0.1, 0.5, size=widths[-1])
+    net.set_transform(in_mu, in_sd, out_mu, out_sd, floor)
+    got = net.predict(x)
+    xn = ((np.log10(np.maximum(x.astype(np.float64), floor)) - in_mu) / in_sd).astype(np.float32)
+    assert np.all(xn[:, -6:] == 0.0)
+    z = net.forward(xn).astype(np.float64)
+    exp = 10.0 ** (z * out_sd + out_mu)
+    # the device takes log10 in FP32: standardised inputs may round to a
+    # neighbouring BF16 value, moving log10 y by a small fraction of a percent
+    assert np.abs(np.log10(got) - np.log10(exp)).max() <= 2e-3
     net.close()
 
 
