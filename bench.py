@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-particles", type=int, default=2048)
     ap.add_argument("--cpu-particles", type=int, default=288)
+    ap.add_argument("--cpu-1core-particles", type=int, default=18)
     ap.add_argument("--particles", type=int, default=None,
                     help="scale the workload to this many particles (profiling cases)")
     ap.add_argument("--variant", type=int, default=None)
@@ -346,6 +347,16 @@ def main():
         cpu = {"value": cupd / cel / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"first {args.cpu_particles} particles of the workload, all 4096 "
                          f"samples x 8 dirs x 1024 omega ({cupd:.3e} updates, {cel:.1f} s)"}
+        if args.cpu_1core_particles > 0:
+            # the same oracle on one core (a smaller bounded sample)
+            oracle.set_num_threads(1)
+            try:
+                c1upd, c1el, _, _ = oracle_sample(args.cpu_1core_particles)
+            finally:
+                oracle.set_num_threads(cores)
+            cpu["one_core"] = {"value": c1upd / c1el / 1e9, "unit": UNIT, "cores": 1,
+                               "sample": f"first {args.cpu_1core_particles} particles "
+                                         f"({c1upd:.3e} updates, {c1el:.1f} s)"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

@@ -29,7 +29,10 @@
  *     betadot_m = (beta_{m+1/2} - beta_{m-1/2})/dt; so sample m needs calls m
  *     and m+1.
  *   - the time integral is a rectangle rule (every sample has weight dt).
- *   - positions in a periodic box of side L are unwrapped by minimum image.
+ *   - positions in a periodic box of side L are unwrapped by minimum image:
+ *     r_m = x_m + L n_m with the integer image count n_0 = 0,
+ *     n_m = n_{m-1} - nearest_integer((x_m - x_{m-1}) / L), i.e. the
+ *     position plus whole box lengths (one rounding, not a running sum).
  *
  * Precision: FP64 throughout, libm sin/cos; build without fast-math and with
  * -ffp-contract=off so that the arithmetic is exactly what is written.
@@ -63,11 +66,10 @@ static void cross3(const double a[3], const double b[3], double out[3])
     out[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-/* Minimum-image difference for a periodic box of side L (L <= 0: none). */
-static double min_image(double d, double L)
+/* Whole box lengths in a displacement d (periodic box of side L; L <= 0: none). */
+static double image_jump(double d, double L)
 {
-    if (L > 0.0) d -= L * nearbyint(d / L);
-    return d;
+    return L > 0.0 ? nearbyint(d / L) : 0.0;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -85,15 +87,14 @@ int rado_samples(int64_t n_calls, int64_t N, const double *x, const double *u,
     if (n_calls < 2 || N < 0 || !(dt > 0.0)) return -1;
     const int64_t n_samp = n_calls - 1;
     for (int64_t j = 0; j < N; ++j) {
+        double img[3] = {0.0, 0.0, 0.0};   /* image count n_m */
         double pos[3];
-        for (int c = 0; c < 3; ++c) pos[c] = x[(0 * 3 + c) * N + j];
         for (int64_t m = 0; m < n_samp; ++m) {
-            /* unwrapped position r_m */
-            if (m > 0) {
-                for (int c = 0; c < 3; ++c) {
-                    double d = x[(m * 3 + c) * N + j] - x[((m - 1) * 3 + c) * N + j];
-                    pos[c] += min_image(d, box_L);
-                }
+            /* unwrapped position r_m = x_m + L n_m */
+            for (int c = 0; c < 3; ++c) {
+                const double xm = x[(m * 3 + c) * N + j];
+                if (m > 0) img[c] -= image_jump(xm - x[((m - 1) * 3 + c) * N + j], box_L);
+                pos[c] = box_L > 0.0 ? xm + box_L * img[c] : xm;
             }
             double um[3], up[3], ubar[3], bm[3], bp[3];
             for (int c = 0; c < 3; ++c) {

@@ -101,6 +101,9 @@ struct rad_ctx {
     cudaEvent_t copy_done[2] = {nullptr, nullptr};
     cudaEvent_t used_done[2] = {nullptr, nullptr};
     int stage_next = 0;
+    // time-segmented ingest: per-segment image-count changes and staged state
+    unsigned char* seg_buf = nullptr;
+    size_t seg_bytes = 0;
     // blocked host path: per-block staging, per-(event, block) work lists
     double* bstage[2] = {nullptr, nullptr};
     size_t bstage_bytes = 0;
@@ -626,6 +629,30 @@ static IngestParams ingest_params(const rad_ctx* c)
     return p;
 }
 
+// Scratch of a time-segmented ingest launch over count particles and n_steps
+// calls (segments of kSegLen calls, a multiple of every anchor interval).
+constexpr int kSegLen = 64;
+static int seg_scratch(rad_ctx* c, int64_t count, int64_t n_steps, IngestParams& p)
+{
+    const int64_t nseg_max = n_steps / kSegLen + 2;
+    const size_t sb = (size_t)9 * count * sizeof(double);
+    const size_t wb = (size_t)nseg_max * 3 * count * sizeof(int32_t);
+    if (c->seg_bytes < sb + wb) {
+        if (c->seg_buf) {
+            CU(cudaStreamSynchronize(c->stream));
+            CU(cudaFree(c->seg_buf));
+            c->seg_buf = nullptr;
+            c->seg_bytes = 0;
+        }
+        CU(cudaMalloc(&c->seg_buf, sb + wb));
+        c->seg_bytes = sb + wb;
+    }
+    p.state_out = reinterpret_cast<double*>(c->seg_buf);
+    p.wind = reinterpret_cast<int32_t*>(c->seg_buf + sb);
+    p.seg_len = kSegLen;
+    return RAD_OK;
+}
+
 // Ingest n steps from device arrays x, u ([n][3][n_in]) starting at step0.
 static int ingest_device(rad_ctx* c, int64_t step0, int64_t n, const double* x, const double* u)
 {
@@ -643,6 +670,8 @@ static int ingest_device(rad_ctx* c, int64_t step0, int64_t n, const double* x, 
         p.u = u + (s - step0) * 3 * c->n_in;
         p.step0 = s;
         p.n_steps = (int32_t)(stop - s);
+        int rs = seg_scratch(c, c->n_in, stop - s, p);
+        if (rs) return rs;
         cudaEvent_t e0 = nullptr;
         if (c->time_ingest) {
             e0 = next_event(c->ing_ev, c->ing_used, true);
@@ -789,6 +818,8 @@ static int ingest_host_blocked(rad_ctx* c, int64_t step0, int64_t n, const doubl
                 p.count = pc;
                 p.ld = pc;
                 p.xoff = p0;
+                rc = seg_scratch(c, pc, m, p);
+                if (rc) return rc;
                 if (c->time_ingest)
                     CU(cudaEventRecord(next_event(c->ing_ev, c->ing_used, true), c->stream));
                 cudaError_t e = launch_ingest(p, c->stream);
@@ -1366,7 +1397,7 @@ void rad_destroy(rad_ctx* c)
     void* bufs[] = {c->slab32, c->slab64, c->anc32, c->x_prev, c->r_prev, c->u_prev,
                     c->d_dirs32, c->d_dirs64, c->d_om32, c->d_nuhi, c->d_nulo,
                     c->d_om64, c->d_wins, c->d_sel, c->d_species, c->acc, c->d_out, c->d_err, c->d_counter,
-                    c->stage[0], c->stage[1], c->bstage[0], c->bstage[1]};
+                    c->stage[0], c->stage[1], c->bstage[0], c->bstage[1], c->seg_buf};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (auto& pr : c->acc_ev) {

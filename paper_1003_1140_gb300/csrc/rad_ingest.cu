@@ -7,9 +7,13 @@
 //   beta_m    = ubar / sqrt(1 + ubar^2),  ubar = (u_{m-1/2} + u_{m+1/2}) / 2,
 //   betadot_m = (beta_{m+1/2} - beta_{m-1/2}) / dt,
 //   g_m       = 1/gamma_m^2 = 1 / (1 + ubar^2).
-// One thread per particle walks the launch's steps in order, keeping the
-// previous raw position, the unwrapped position and u_{s-3/2} in registers
-// and in the per-particle state arrays between launches.
+// A thread walks one particle through one time segment of the launch's steps,
+// keeping the previous raw position, the image count n (the unwrapped position
+// is r = x + L n) and u_{s-3/2} in registers; the per-particle state arrays
+// carry them between launches.  Segments after the first start at
+// anchor-aligned samples; their starting image count is the launch's initial
+// count plus the integer changes of the earlier segments (wind_kernel), so the
+// split in time changes no result.
 #include "rad_internal.cuh"
 
 namespace rad {
@@ -18,10 +22,62 @@ namespace rad {
 // that did not cross the boundary has |d| <= L/2, where that is d itself
 // (rint(d / L) = +-0 exactly); only a crossing pays for the FP64 division,
 // which this GPU runs on its 1/64-rate FP64 pipe.  Same value in every case.
-__device__ __forceinline__ double min_image(double d, double L, double half_L)
+__device__ __forceinline__ double image_jump(double d, double L, double half_L)
 {
-    if (!(L > 0.0) || fabs(d) <= half_L) return d;
-    return d - L * rint(d / L);
+    if (!(L > 0.0) || fabs(d) <= half_L) return 0.0;
+    return rint(d / L);
+}
+
+// Calls [s_begin, s_end) of segment g of the launch.
+__device__ __forceinline__ void segment_range(const IngestParams& p, int g, int64_t& s_begin,
+                                              int64_t& s_end)
+{
+    const int64_t end = p.step0 + p.n_steps;
+    if (p.n_seg <= 1) {
+        s_begin = p.step0;
+        s_end = end;
+        return;
+    }
+    s_begin = g == 0 ? p.step0 : p.seg_first + (int64_t)(g - 1) * p.seg_len;
+    const int64_t e = p.seg_first + (int64_t)g * p.seg_len;
+    s_end = e < end ? e : end;
+}
+
+// Change of the image count over each segment but the last (box_L > 0).
+__global__ void __launch_bounds__(256) wind_kernel(const IngestParams p)
+{
+    const int64_t cnt = p.count ? p.count : p.n_in - p.first;
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= cnt * (p.n_seg - 1)) return;
+    const int g = (int)(q / cnt);
+    const int64_t k = q - (int64_t)g * cnt, i = p.first + k;
+    const int64_t ld = p.ld ? p.ld : p.n_in;
+    const int64_t xi = i - p.xoff;
+    int sp = 0;
+    while (sp + 1 < p.n_species && i >= p.in_off[sp + 1]) ++sp;
+    const int64_t col = p.col_off[sp] + (i - p.in_off[sp]);
+    int64_t s_begin, s_end;
+    segment_range(p, g, s_begin, s_end);
+    const double half_L = 0.5 * p.box_L;
+    double xp[3];
+    bool have = true;
+    if (s_begin > p.step0) {
+        for (int c = 0; c < 3; ++c) xp[c] = p.x[(s_begin - 1 - p.step0) * 3 * ld + c * ld + xi];
+    } else if (p.step0 > 0) {
+        for (int c = 0; c < 3; ++c) xp[c] = p.x_prev[c * p.ncols + col];
+    } else {
+        have = false;                       // call 0 has no predecessor
+    }
+    int32_t dn[3] = {0, 0, 0};
+    for (int64_t s = s_begin; s < s_end; ++s) {
+        for (int c = 0; c < 3; ++c) {
+            const double xn = p.x[(s - p.step0) * 3 * ld + c * ld + xi];
+            if (have) dn[c] -= (int32_t)image_jump(xn - xp[c], p.box_L, half_L);
+            xp[c] = xn;
+        }
+        have = true;
+    }
+    for (int c = 0; c < 3; ++c) p.wind[((int64_t)g * 3 + c) * cnt + k] = dn[c];
 }
 
 // Selector bits of a sample: box tests on the position as handed over, cone
@@ -49,33 +105,53 @@ __device__ uint32_t selector_bits(const IngestParams& p, const double x[3], cons
     return bits;
 }
 
-__global__ void __launch_bounds__(256) ingest_kernel(const IngestParams p)
+// 64-thread blocks (launch_ingest), at least 8 resident per SM: the FP64-bound
+// loop needs the warps to hide its latency more than it needs registers.
+__global__ void __launch_bounds__(64, 8) ingest_kernel(const IngestParams p)
 {
-    const int64_t i = p.first + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t cnt = p.count ? p.count : p.n_in - p.first;
-    if (i >= p.first + cnt) return;
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int nseg = p.n_seg > 1 ? p.n_seg : 1;
+    if (q >= cnt * nseg) return;
+    const int g = (int)(q / cnt);                // time segment
+    const int64_t k = q - (int64_t)g * cnt;
+    const int64_t i = p.first + k;
     const int64_t ld = p.ld ? p.ld : p.n_in;    // input particle stride
     const int64_t xi = i - p.xoff;              // input column of particle i
+    int64_t s_begin, s_end;
+    segment_range(p, g, s_begin, s_end);
+    const int n_loc = (int)(s_end - s_begin);   // calls of this thread
+    const int64_t t0 = s_begin - p.step0;       // its first input row
     int sp = 0;
     while (sp + 1 < p.n_species && i >= p.in_off[sp + 1]) ++sp;
     const int64_t col = p.col_off[sp] + (i - p.in_off[sp]);
     const int64_t nc = p.ncols;
     const int64_t tile = col / kTileP, pp = col % kTileP;
 
-    double xp[3], rp[3], up[3], ra[3];
+    double xp[3], off[3], rp[3], up[3], ra[3];   // off = L n (n the image count), exact
     const double half_L = 0.5 * p.box_L;
-    bool have_state = p.step0 > 0;
+    const bool box = p.box_L > 0.0;
+    bool have_state = s_begin > 0;
     // ring slot, position in the anchor block and anchor block of the next
     // sample m (nsub = 1), advanced by counters instead of 64-bit divisions
-    int64_t m_next = p.step0 > 0 ? p.step0 - 1 : 0;
+    int64_t m_next = s_begin > 0 ? s_begin - 1 : 0;
     // (nblk is 0 for an FP64 ring, which has no anchors)
     int64_t slot_n = m_next % p.ring, kpos_n = m_next % p.K;
     int64_t blk_n = p.nblk > 0 ? (m_next / p.K) % p.nblk : 0;
     if (have_state) {
         for (int c = 0; c < 3; ++c) {
-            xp[c] = p.x_prev[c * nc + col];
-            rp[c] = p.r_prev[c * nc + col];
-            up[c] = p.u_prev[c * nc + col];
+            // image count at the launch start, plus the earlier segments' changes
+            double n0 = p.step0 > 0 ? p.r_prev[c * nc + col] : 0.0;
+            for (int h = 0; h < g; ++h) n0 += (double)p.wind[((int64_t)h * 3 + c) * cnt + k];
+            off[c] = box ? p.box_L * n0 : 0.0;
+            if (g == 0) {
+                xp[c] = p.x_prev[c * nc + col];
+                up[c] = p.u_prev[c * nc + col];
+            } else {
+                xp[c] = p.x[(t0 - 1) * 3 * ld + c * ld + xi];
+                up[c] = p.u[(t0 - 1) * 3 * ld + c * ld + xi];
+            }
+            rp[c] = xp[c] + off[c];
         }
     }
     bool have_anchor = false;
@@ -84,19 +160,19 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestParams p)
     // the next step's inputs are loaded while this step is being processed
     double xq[3], uq[3];
     for (int c = 0; c < 3; ++c) {
-        xq[c] = p.n_steps > 0 ? p.x[c * ld + xi] : 0.0;
-        uq[c] = p.n_steps > 0 ? p.u[c * ld + xi] : 0.0;
+        xq[c] = n_loc > 0 ? p.x[t0 * 3 * ld + c * ld + xi] : 0.0;
+        uq[c] = n_loc > 0 ? p.u[t0 * 3 * ld + c * ld + xi] : 0.0;
     }
-    for (int t = 0; t < p.n_steps; ++t) {
-        const int64_t s = p.step0 + t;
+    for (int t = 0; t < n_loc; ++t) {
+        const int64_t s = s_begin + t;
         double xn[3], un[3], rn[3];
         for (int c = 0; c < 3; ++c) {
             xn[c] = xq[c];
             un[c] = uq[c];
         }
-        if (t + 1 < p.n_steps) {
-            const double* xs = p.x + (int64_t)(t + 1) * 3 * ld;
-            const double* us = p.u + (int64_t)(t + 1) * 3 * ld;
+        if (t + 1 < n_loc) {
+            const double* xs = p.x + (t0 + t + 1) * 3 * ld;
+            const double* us = p.u + (t0 + t + 1) * 3 * ld;
             for (int c = 0; c < 3; ++c) {
                 xq[c] = xs[c * ld + xi];
                 uq[c] = us[c * ld + xi];
@@ -108,13 +184,19 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestParams p)
         if (s == 0) {
             for (int c = 0; c < 3; ++c) {
                 xp[c] = xn[c];
+                off[c] = 0.0;
                 rp[c] = xn[c];
                 up[c] = un[c];
             }
             continue;
         }
-        // unwrapped position of this call
-        for (int c = 0; c < 3; ++c) rn[c] = rp[c] + min_image(xn[c] - xp[c], p.box_L, half_L);
+        // unwrapped position of this call: r = x + L n, n counting box crossings
+        // (L n, exact, changes only at a crossing)
+        for (int c = 0; c < 3; ++c) {
+            const double jump = image_jump(xn[c] - xp[c], p.box_L, half_L);
+            if (jump != 0.0) off[c] -= p.box_L * jump;      // exact: integer multiples of L
+            rn[c] = xn[c] + off[c];
+        }
 
         // sample m = s - 1: r_m = rp, u_{m-1/2} = up, u_{m+1/2} = un
         const int64_t m = s - 1;
@@ -280,12 +362,40 @@ __global__ void __launch_bounds__(256) ingest_kernel(const IngestParams p)
             up[c] = un[c];
         }
     }
-    for (int c = 0; c < 3; ++c) {
-        p.x_prev[c * nc + col] = xp[c];
-        p.r_prev[c * nc + col] = rp[c];
-        p.u_prev[c * nc + col] = up[c];
+    if (g == nseg - 1) {                        // the launch's last segment carries the state on
+        if (nseg > 1) {
+            // segment 0 may still be reading the state arrays: stage it
+            for (int c = 0; c < 3; ++c) {
+                p.state_out[c * cnt + k] = xp[c];
+                p.state_out[(3 + c) * cnt + k] = box ? off[c] / p.box_L : 0.0;   // exact
+                p.state_out[(6 + c) * cnt + k] = up[c];
+            }
+        } else {
+            for (int c = 0; c < 3; ++c) {
+                p.x_prev[c * nc + col] = xp[c];
+                p.r_prev[c * nc + col] = box ? off[c] / p.box_L : 0.0;
+                p.u_prev[c * nc + col] = up[c];
+            }
+        }
     }
     if (bad) atomicOr(p.err_word, kErrNaN);
+}
+
+// The staged carry-over state of a segmented launch into the state arrays.
+__global__ void store_state(const IngestParams p)
+{
+    const int64_t cnt = p.count ? p.count : p.n_in - p.first;
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= cnt) return;
+    const int64_t i = p.first + k;
+    int sp = 0;
+    while (sp + 1 < p.n_species && i >= p.in_off[sp + 1]) ++sp;
+    const int64_t col = p.col_off[sp] + (i - p.in_off[sp]);
+    for (int c = 0; c < 3; ++c) {
+        p.x_prev[c * p.ncols + col] = p.state_out[c * cnt + k];
+        p.r_prev[c * p.ncols + col] = p.state_out[(3 + c) * cnt + k];
+        p.u_prev[c * p.ncols + col] = p.state_out[(6 + c) * cnt + k];
+    }
 }
 
 const void* ingest_kernel_ptr() { return reinterpret_cast<const void*>(&ingest_kernel); }
@@ -294,13 +404,34 @@ cudaError_t launch_ingest(const IngestParams& p, cudaStream_t st)
 {
     const int64_t cnt = p.count ? p.count : p.n_in - p.first;
     if (cnt <= 0 || p.n_steps == 0) return cudaSuccess;
+    IngestParams q = p;
+    q.n_seg = 1;
+    // time segments only when the particles alone leave the GPU idle: with
+    // 32,768 or more one thread per particle already keeps the FP64 pipes of
+    // all SMs busy, and the segments' extra pass only adds work (measured)
+    constexpr int64_t kSegMaxParticles = 32768;
+    if (p.wind && p.state_out && p.seg_len > 0 && cnt < kSegMaxParticles) {
+        // boundaries at calls 1 + j seg_len strictly inside (step0, step0 + n_steps)
+        const int64_t end = p.step0 + p.n_steps;
+        const int64_t j0 = p.step0 < 1 ? 0 : (p.step0 - 1) / p.seg_len + 1;
+        const int64_t first = 1 + j0 * p.seg_len;
+        if (first < end) {
+            q.seg_first = first;
+            q.n_seg = (int32_t)(1 + (end - first + p.seg_len - 1) / p.seg_len);
+        }
+    }
     // one thread per particle, small blocks: the kernel is bound by its FP64
     // work per SM, so the blocks must spread evenly over all 152 SMs (256-thread
     // blocks left 65,536 particles at two blocks on most SMs and one on the rest,
     // and a 16,384-particle share on 64 SMs)
     const int threads = 64;
-    const int64_t blocks = (cnt + threads - 1) / threads;
-    ingest_kernel<<<(unsigned)blocks, threads, 0, st>>>(p);
+    if (q.n_seg > 1 && q.box_L > 0.0) {
+        const int64_t nw = cnt * (q.n_seg - 1);
+        wind_kernel<<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(q);
+    }
+    const int64_t blocks = (cnt * q.n_seg + threads - 1) / threads;
+    ingest_kernel<<<(unsigned)blocks, threads, 0, st>>>(q);
+    if (q.n_seg > 1) store_state<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(q);
     return cudaGetLastError();
 }
 

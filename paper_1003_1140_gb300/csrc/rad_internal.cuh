@@ -216,7 +216,7 @@ struct IngestParams {
     double dt;
     double box_L;           // 0: no unwrapping
     double* x_prev;         // [3][ncols] raw x of the previous call
-    double* r_prev;         // [3][ncols] unwrapped x of the previous call
+    double* r_prev;         // [3][ncols] image count n of the previous call (r = x + L n)
     double* u_prev;         // [3][ncols] u of the previous call
     float* slab32;          // FP32 ring or nullptr
     double* slab64;         // FP64 ring or nullptr
@@ -241,6 +241,16 @@ struct IngestParams {
     int64_t count;
     int64_t ld;
     int64_t xoff;
+    // time segments (one thread per particle and segment): segment 0 starts at
+    // step0, segment g >= 1 at seg_first + (g - 1) seg_len (calls 1 + j seg_len:
+    // anchor-aligned samples); wind [n_seg - 1][3][count] receives each
+    // segment's change of the image count.  n_seg <= 1: one thread per particle.
+    int64_t seg_first;
+    int32_t seg_len;
+    int32_t n_seg;
+    int32_t* wind;
+    double* state_out;      // [9][count]: the last segment's carry-over state,
+                            // stored to x_prev/r_prev/u_prev after the launch
 };
 
 struct Accum32Params {
