@@ -40,8 +40,8 @@ METRIC = "G particle·step·ω·n updates/s, FP32 split vs FP64 GPU at ≤1e-4 r
 # in profiles/accum32_workload2_4096p.md (4096 particles, this workload's samples,
 # directions and omegas), valid while the kernel source and its work-list builder are
 # the ones that were captured; traffic scales with the particle count.
-TRAFFIC_CAPTURE = {"sources_sha256": "5365a092915ef071bce500b57e2fa51314c31a378ccf018066fe1f1686301c50",
-                   "bytes_per_launch": 777.483264e6, "particles": 4096}
+TRAFFIC_CAPTURE = {"sources_sha256": "69a8457e8831f3f4dc4ff7968d4b37ab5dd361cbbb36073550d5ff6ea02e9574",
+                   "bytes_per_launch": 782.355712e6, "particles": 4096}
 UNIT = "G updates/s"
 WORKLOAD = 2
 
