@@ -385,3 +385,27 @@ def test_host_blocked_transfer(precision, coherent):
     ref = oracle.spectra(X, U, w.dt, w.dirs, w.grids, w.windows, [(2050, -1.0)],
                          coherent=coherent, box_L=w.L)
     _check(host, ref, 1e-10 if precision == R.RAD_FP64 else 1e-4, per_direction=True)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_host_blocked_transfer_with_subcycling_and_selector(precision):
+    """The particle-blocked host transfer with 3 sub-samples per PIC sample
+    and a region selector on one window, against the oracle's sub-cycled,
+    selected sum (2050 particles, 1 MiB staging cap, windows closing inside
+    the batch; the particle blocks' ingest is also split in time)."""
+    R = _rad()
+    w = trajgen.Workload("blocked-sub", [(2050, -1.0, 1.0, 3.0)], 161, 0.05,
+                         np.array([[0.0, 1.0, 0.0], [0.6, 0.0, 0.8]]),
+                         [trajgen.log_grid(0.1, 200.0, 48)],
+                         [(0, 160, 1, 0), (40, 100, 1, 0)], b_rms=0.3)
+    X, U = w.trajectory_numpy()
+    sels = [{"kind": "box", "lo": [0, 5, 0], "hi": [40, 35, 30]}]
+    wsel = [-1, 0]
+    ref = oracle.spectra(X, U, w.dt, w.dirs, w.grids, w.windows, [(2050, -1.0)], box_L=w.L,
+                         selectors=sels, window_selector=wsel, subcycle=3)
+    with R.Radiation(w.dirs, w.grids, w.dt, [(2050, -1.0, 1.0)], w.windows, precision=precision,
+                     box_L=w.L, options={"subcycle": 3, "host_stage_mib": 1}) as r:
+        r.set_selectors(sels, wsel)
+        r.accumulate_steps(0, np.ascontiguousarray(X), np.ascontiguousarray(U))
+        got = r.finalize()
+    _check(got, ref, 1e-10 if precision == 0 else 1e-4, per_direction=True)
