@@ -124,7 +124,8 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(w, {"path": "FP64 CPU oracle (C, libm, OpenMP)"}),
+            "config": workload_config(w, {"path": "FP64 CPU oracle (C, libm, OpenMP)",
+                                          "l2": "not applicable: CPU oracle on host memory"}),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,

@@ -19,12 +19,13 @@ def _periodic_diff(a, b, L):
     return d - L * np.round(d / L)
 
 
-def test_pic_matches_reference_pic():
-    """20 steps of a small two-stream box, field and particle state against the
-    NumPy reference from the same initial state (the GPU's atomic current sums
-    differ in the last bits only)."""
+@pytest.mark.parametrize("mass_ratio", [64.0, 1.0])
+def test_pic_matches_reference_pic(mass_ratio):
+    """20 steps of a small two-stream box (baryonic or pair partners), field and
+    particle state against the NumPy reference from the same initial state (the
+    GPU's atomic current sums differ in the last bits only)."""
     from paper_1003_1140_gb300 import pic
-    ts = trajgen.TwoStream(n=16, ppc=2, gamma=3.0, u_th=0.05, seed=21)
+    ts = trajgen.TwoStream(n=16, ppc=2, gamma=3.0, u_th=0.05, mass_ratio=mass_ratio, seed=21)
     X, U, q, m, w = ts.particles()
     g = ref.Grid(ts.n, ts.d, ts.dt)
     E = np.zeros((3, ts.n, ts.n))
@@ -93,7 +94,8 @@ def _rad_setup(N_track, S):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_in_situ_spectrum_matches_oracle(precision):
+@pytest.mark.parametrize("coherent", [False, True])
+def test_in_situ_spectrum_matches_oracle(precision, coherent):
     """The PIC hands the first 96 electrons to the diagnostic every step (device
     buffers, no host copy on the path); the spectra equal the oracle's on the
     recorded histories of the same particles: <= 1e-10 (FP64), <= 1e-4 (FP32 split)."""
@@ -108,6 +110,7 @@ def test_in_situ_spectrum_matches_oracle(precision):
     hx, hu = [], []
     with pic.Pic.two_stream(ts) as p, \
             R.Radiation(dirs, grids, ts.dt, [(Nt, -1.0, 1.0)], windows, precision=prec,
+                        mode=R.RAD_COHERENT if coherent else R.RAD_INCOHERENT,
                         box_L=ts.L) as r:
         for s in range(S + 1):
             p.tracked(0, Nt, xt, ut)
@@ -118,7 +121,7 @@ def test_in_situ_spectrum_matches_oracle(precision):
                 p.step(1)
         got = r.finalize()
     exp = oracle.spectra(np.stack(hx), np.stack(hu), ts.dt, dirs, grids, windows, species,
-                         box_L=ts.L)
+                         coherent=coherent, box_L=ts.L)
     tol = 1e-10 if precision == "fp64" else 1e-4
     for gw, ew in zip(got, exp):
         for d in range(len(dirs)):
