@@ -18,10 +18,11 @@
 
 namespace rad {
 
-// Nearest periodic image of a displacement: d - L rint(d / L).  A particle
-// that did not cross the boundary has |d| <= L/2, where that is d itself
-// (rint(d / L) = +-0 exactly); only a crossing pays for the FP64 division,
-// which this GPU runs on its 1/64-rate FP64 pipe.  Same value in every case.
+// Whole box lengths in a displacement d, rint(d / L): the change of the image
+// count (its nearest periodic image is d - L rint(d / L)).  A particle that did
+// not cross the boundary has |d| <= L/2, where that is 0 exactly; only a
+// crossing pays for the FP64 division, which this GPU runs on its 1/64-rate
+// FP64 pipe.  Same value in every case.
 __device__ __forceinline__ double image_jump(double d, double L, double half_L)
 {
     if (!(L > 0.0) || fabs(d) <= half_L) return 0.0;
