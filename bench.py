@@ -291,8 +291,15 @@ def main():
     # end to end through the public API with host buffers (pinned), H2D/D2H inside
     e2e = None
     if not args.no_e2e:
-        Xh = torch.empty(X.shape, dtype=torch.float64, pin_memory=True)
-        Uh = torch.empty(U.shape, dtype=torch.float64, pin_memory=True)
+        host_mem = "pinned"
+        try:
+            Xh = torch.empty(X.shape, dtype=torch.float64, pin_memory=True)
+            Uh = torch.empty(U.shape, dtype=torch.float64, pin_memory=True)
+        except RuntimeError:
+            # many ranks on one node may not be able to lock 13 GB each
+            host_mem = "pageable"
+            Xh = torch.empty(X.shape, dtype=torch.float64)
+            Uh = torch.empty(U.shape, dtype=torch.float64)
         Xh.copy_(X)
         Uh.copy_(U)
         outh = np.empty(ctx.spectrum_size())
@@ -317,7 +324,7 @@ def main():
             el = float(t.item())
         e2e = {"value": world * upd / (el / ke) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(Xh.numel() * 8 + Uh.numel() * 8),
-               "d2h_bytes_per_step": int(outh.size * 8)}
+               "d2h_bytes_per_step": int(outh.size * 8), "host_memory": host_mem}
         del Xh, Uh
 
     # FP64 GPU path on a particle subset, and the FP32 split error against it
