@@ -409,3 +409,30 @@ def test_host_blocked_transfer_with_subcycling_and_selector(precision):
         r.accumulate_steps(0, np.ascontiguousarray(X), np.ascontiguousarray(U))
         got = r.finalize()
     _check(got, ref, 1e-10 if precision == 0 else 1e-4, per_direction=True)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("host", [False, True])
+def test_batches_across_calls(precision, host):
+    """The same 181 calls handed over in three batches of uneven length (67, 70,
+    44), windows opening in one batch and closing in another: the per-particle
+    ingest state (raw position, image count, u) carries across batches through
+    the blocked host transfer and the time-segmented ingest alike."""
+    R = _rad()
+    w = trajgen.Workload("batches", [(2050, -1.0, 1.0, 3.0)], 181, 0.05,
+                         np.array([[0.0, 1.0, 0.0], [0.6, 0.0, 0.8]]),
+                         [trajgen.log_grid(0.1, 200.0, 48)],
+                         [(0, 180, 1, 0), (50, 120, 1, 0), (10, 60, 1, 0)], b_rms=0.3)
+    X, U = w.trajectory_numpy()
+    ref = oracle.spectra(X, U, w.dt, w.dirs, w.grids, w.windows, [(2050, -1.0)], box_L=w.L)
+    with R.Radiation(w.dirs, w.grids, w.dt, [(2050, -1.0, 1.0)], w.windows, precision=precision,
+                     box_L=w.L, options={"host_stage_mib": 1}) as r:
+        s = 0
+        for n in (67, 70, 44):
+            xs, us = np.ascontiguousarray(X[s:s + n]), np.ascontiguousarray(U[s:s + n])
+            if not host:
+                xs, us = torch.as_tensor(xs, device="cuda"), torch.as_tensor(us, device="cuda")
+            r.accumulate_steps(s, xs, us)
+            s += n
+        got = r.finalize()
+    _check(got, ref, 1e-10 if precision == 0 else 1e-4, per_direction=True)
