@@ -634,7 +634,7 @@ static IngestParams ingest_params(const rad_ctx* c)
 constexpr int kSegLen = 64;
 static int seg_scratch(rad_ctx* c, int64_t count, int64_t n_steps, IngestParams& p)
 {
-    const int64_t nseg_max = n_steps / kSegLen + 2;
+    const int64_t nseg_max = std::min<int64_t>(n_steps / kSegLen + 2, 257);   // launch_ingest caps at 256
     const size_t sb = (size_t)9 * count * sizeof(double);
     const size_t wb = (size_t)nseg_max * 3 * count * sizeof(int32_t);
     if (c->seg_bytes < sb + wb) {

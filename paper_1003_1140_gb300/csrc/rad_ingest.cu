@@ -413,12 +413,19 @@ cudaError_t launch_ingest(const IngestParams& p, cudaStream_t st)
     constexpr int64_t kSegMaxParticles = 32768;
     if (p.wind && p.state_out && p.seg_len > 0 && cnt < kSegMaxParticles) {
         // boundaries at calls 1 + j seg_len strictly inside (step0, step0 + n_steps)
+        // at most kMaxSeg segments (each thread sums the earlier segments' counts):
+        // longer batches get longer segments, still multiples of seg_len
+        constexpr int64_t kMaxSeg = 256;
         const int64_t end = p.step0 + p.n_steps;
-        const int64_t j0 = p.step0 < 1 ? 0 : (p.step0 - 1) / p.seg_len + 1;
-        const int64_t first = 1 + j0 * p.seg_len;
+        int64_t len = p.seg_len;
+        const int64_t span = p.n_steps / (kMaxSeg - 1) + 1;
+        if (span > len) len = (span + p.seg_len - 1) / p.seg_len * p.seg_len;
+        const int64_t j0 = p.step0 < 1 ? 0 : (p.step0 - 1) / len + 1;
+        const int64_t first = 1 + j0 * len;
         if (first < end) {
+            q.seg_len = (int32_t)len;
             q.seg_first = first;
-            q.n_seg = (int32_t)(1 + (end - first + p.seg_len - 1) / p.seg_len);
+            q.n_seg = (int32_t)(1 + (end - first + len - 1) / len);
         }
     }
     // one thread per particle, small blocks: the kernel is bound by its FP64
