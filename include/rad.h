@@ -125,8 +125,8 @@ typedef struct {
                               [1]: MIX variant, frequencies of each thread on the
                               FMA-pipe polynomial (0: 2 of 8, 4 of 16); after the
                               first step rad_get_options reports the kernel build
-                              in use here (0 for SFU); [2]: host inputs of one
-                              species, eager windows: MiB per staging buffer of the
+                              in use here (0 for SFU); [2]: host inputs with
+                              eager windows: MiB per staging buffer of the
                               particle-blocked transfer (0: 8192); others must be 0 */
 } rad_options;
 
@@ -183,8 +183,8 @@ int rad_accumulate(rad_ctx *ctx, int64_t step, const double *x, const double *u)
  * rad_accumulate_steps -- hand over n_steps consecutive steps at once:
  * x, u are [n_steps][3][N_total] FP64.  Equivalent to n_steps calls of
  * rad_accumulate, with fewer launches.  Host inputs are copied by the library
- * (the caller may reuse them when this returns); with one species, eager
- * windows and at least 64 steps and 2048 particles, the particle axis is
+ * (the caller may reuse them when this returns); with eager windows and at
+ * least 64 steps and 2048 particles, the particle axis (every species) is
  * streamed in blocks so that the transfer of later particles overlaps the
  * accumulation of earlier ones (results equal up to FP64 summation order).
  */

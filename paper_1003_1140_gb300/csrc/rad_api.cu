@@ -216,11 +216,14 @@ static int freq_tile(const rad_ctx* c)
 }
 
 // Build the work items of one event (set of windows) and sort by cost.
-// Work items of an event's windows; with [tlo, thi) only the particle tiles in
-// that range (the blocked host path; single species), the groups sized for the
-// range so that every list balances over the GPU.
-static void build_items(rad_ctx* c, Event& ev, int total_blocks, int tlo = 0, int thi = INT_MAX)
+// Work items of an event's windows; with `ranges` only the particle tiles
+// [first, second) of each species (the blocked host path), the groups sized for
+// those tiles so that every list balances over the GPU.
+static void build_items(rad_ctx* c, Event& ev, int total_blocks,
+                        const std::vector<std::pair<int, int>>* ranges = nullptr)
 {
+    auto lo_of = [&](int s) { return ranges ? (*ranges)[s].first : 0; };
+    auto hi_of = [&](int s) { return ranges ? (*ranges)[s].second : INT_MAX; };
     const int ftl = freq_tile(c);
     const int ch = chunk_len(c);
     // total (tile x direction x ftile) units, to size the particle groups
@@ -231,7 +234,7 @@ static void build_items(rad_ctx* c, Event& ev, int total_blocks, int tlo = 0, in
         for (int s = 0; s < c->n_species; ++s)
             if ((W.species_mask >> s) & 1u) {
                 const int nts = (int)((c->species[s].count + kTileP - 1) / kTileP);
-                const int in_range = std::max(0, std::min(nts, thi) - std::max(0, tlo));
+                const int in_range = std::max(0, std::min(nts, hi_of(s)) - std::max(0, lo_of(s)));
                 units += (double)in_range * nft * c->D;
             }
     }
@@ -247,11 +250,11 @@ static void build_items(rad_ctx* c, Event& ev, int total_blocks, int tlo = 0, in
         for (int s = 0; s < c->n_species; ++s) {
             if (!((W.species_mask >> s) & 1u) || c->species[s].count == 0) continue;
             const int nt = (int)((c->species[s].count + kTileP - 1) / kTileP);
-            const int t_end = std::min(nt, thi);
+            const int t_end = std::min(nt, hi_of(s));
             // tile-group-major: the items that read the same particles
             // (all directions and frequency tiles) are adjacent in the list,
             // so they run at about the same time and share L2
-            for (int t0 = std::max(0, tlo); t0 < t_end; t0 += G)
+            for (int t0 = std::max(0, lo_of(s)); t0 < t_end; t0 += G)
                 for (int d = 0; d < c->D; ++d)
                     for (int f = 0; f < nft; ++f) {
                         WorkItem it{w, d, f, s, t0, std::min(G, t_end - t0)};
@@ -726,9 +729,29 @@ static std::vector<int> block_bounds(int nt)
     return b;
 }
 
-static int blocked_lists(rad_ctx* c, const std::vector<int>& bounds)
+// Tile boundaries of the blocks for every species: the geometric schedule of
+// the whole particle axis applied to each species in proportion.
+static std::vector<std::vector<int>> species_bounds(const rad_ctx* c)
 {
-    const int nblocks = (int)bounds.size() - 1;
+    int nt_all = 0;
+    std::vector<int> nts(c->n_species);
+    for (int s = 0; s < c->n_species; ++s) {
+        nts[s] = (int)((c->species[s].count + kTileP - 1) / kTileP);
+        nt_all += nts[s];
+    }
+    const std::vector<int> g = block_bounds(std::max(1, nt_all));
+    std::vector<std::vector<int>> b(c->n_species);
+    for (int s = 0; s < c->n_species; ++s) {
+        b[s].resize(g.size());
+        for (size_t i = 0; i < g.size(); ++i)
+            b[s][i] = i + 1 == g.size() ? nts[s] : (int)((int64_t)g[i] * nts[s] / nt_all);
+    }
+    return b;
+}
+
+static int blocked_lists(rad_ctx* c, const std::vector<std::vector<int>>& bounds)
+{
+    const int nblocks = (int)bounds[0].size() - 1;
     if (c->blk_count == nblocks) return RAD_OK;
     for (auto& row : c->blk_events)
         for (auto& ev : row) cudaFree(ev.d_items);
@@ -739,7 +762,9 @@ static int blocked_lists(rad_ctx* c, const std::vector<int>& bounds)
             Event& ev = c->blk_events[e][b];
             ev.call = c->events[e].call;
             ev.wins = c->events[e].wins;
-            build_items(c, ev, total_blocks, bounds[b], bounds[b + 1]);
+            std::vector<std::pair<int, int>> ranges(c->n_species);
+            for (int s = 0; s < c->n_species; ++s) ranges[s] = {bounds[s][b], bounds[s][b + 1]};
+            build_items(c, ev, total_blocks, &ranges);
             if (!ev.items.empty()) {
                 CU(cudaMalloc(&ev.d_items, ev.items.size() * sizeof(WorkItem)));
                 CU(cudaMemcpy(ev.d_items, ev.items.data(), ev.items.size() * sizeof(WorkItem),
@@ -759,12 +784,25 @@ static int ingest_host_blocked(rad_ctx* c, int64_t step0, int64_t n, const doubl
                                const double* u)
 {
     const int64_t N = c->n_in;
-    const int nt = (int)((N + kTileP - 1) / kTileP);
-    const std::vector<int> bounds = block_bounds(nt);
-    const int nblocks = (int)bounds.size() - 1;
-    int64_t ppb = 0;                                                  // largest block
-    for (int b = 0; b < nblocks; ++b)
-        ppb = std::max<int64_t>(ppb, (int64_t)(bounds[b + 1] - bounds[b]) * kTileP);
+    const int S = c->n_species;
+    const std::vector<std::vector<int>> bounds = species_bounds(c);
+    const int nblocks = (int)bounds[0].size() - 1;
+    // particles of species s in block b: species-local [lo, hi)
+    auto range = [&](int s, int b, int64_t& lo, int64_t& cnt) {
+        lo = (int64_t)bounds[s][b] * kTileP;
+        cnt = std::max<int64_t>(0, std::min<int64_t>((int64_t)bounds[s][b + 1] * kTileP,
+                                                     c->species[s].count) - lo);
+    };
+    int64_t ppb = 1;                                                  // largest block
+    for (int b = 0; b < nblocks; ++b) {
+        int64_t tot = 0;
+        for (int s = 0; s < S; ++s) {
+            int64_t lo, cnt;
+            range(s, b, lo, cnt);
+            tot += cnt;
+        }
+        ppb = std::max(ppb, tot);
+    }
     int rc = blocked_lists(c, bounds);
     if (rc) return rc;
     const size_t cap = c->opt.reserved[2] > 0 ? (size_t)c->opt.reserved[2] << 20 : kBlockStageBytes;
@@ -791,43 +829,58 @@ static int ingest_host_blocked(rad_ctx* c, int64_t step0, int64_t n, const doubl
         if (itv != c->event_at.end() && itv->first < end) stop = itv->first + 1;
         const int ev_idx = (itv != c->event_at.end() && itv->first == stop - 1) ? itv->second : -1;
         for (int b = 0; b < nblocks; ++b) {
-            const int64_t p0 = (int64_t)bounds[b] * kTileP;
-            const int64_t pc = std::min<int64_t>((int64_t)bounds[b + 1] * kTileP, N) - p0;
             for (int64_t t = s; t < stop; t += chunk) {
                 const int64_t m = std::min(chunk, stop - t);
                 const int buf = c->stage_next;
                 c->stage_next ^= 1;
-                double* sx = c->bstage[buf];
-                double* su = sx + m * 3 * pc;
                 CU(cudaStreamWaitEvent(c->copy_stream, c->used_done[buf], 0));
-                const double* xs = x + ((t - step0) * 3) * N + p0;
-                const double* us = u + ((t - step0) * 3) * N + p0;
-                CU(cudaMemcpy2DAsync(sx, pc * sizeof(double), xs, N * sizeof(double),
-                                     pc * sizeof(double), (size_t)(m * 3), cudaMemcpyHostToDevice,
-                                     c->copy_stream));
-                CU(cudaMemcpy2DAsync(su, pc * sizeof(double), us, N * sizeof(double),
-                                     pc * sizeof(double), (size_t)(m * 3), cudaMemcpyHostToDevice,
-                                     c->copy_stream));
+                // one region per species: x then u, [m][3][count] each
+                double* region = c->bstage[buf];
+                for (int sp = 0; sp < S; ++sp) {
+                    int64_t lo, cnt;
+                    range(sp, b, lo, cnt);
+                    if (cnt == 0) continue;
+                    const int64_t g0 = c->in_off[sp] + lo;              // input column
+                    double* sx = region;
+                    double* su = sx + m * 3 * cnt;
+                    region = su + m * 3 * cnt;
+                    const double* xs = x + ((t - step0) * 3) * N + g0;
+                    const double* us = u + ((t - step0) * 3) * N + g0;
+                    CU(cudaMemcpy2DAsync(sx, cnt * sizeof(double), xs, N * sizeof(double),
+                                         cnt * sizeof(double), (size_t)(m * 3),
+                                         cudaMemcpyHostToDevice, c->copy_stream));
+                    CU(cudaMemcpy2DAsync(su, cnt * sizeof(double), us, N * sizeof(double),
+                                         cnt * sizeof(double), (size_t)(m * 3),
+                                         cudaMemcpyHostToDevice, c->copy_stream));
+                }
                 CU(cudaEventRecord(c->copy_done[buf], c->copy_stream));
                 CU(cudaStreamWaitEvent(c->stream, c->copy_done[buf], 0));
-                p.x = sx;
-                p.u = su;
-                p.step0 = t;
-                p.n_steps = (int32_t)m;
-                p.first = p0;
-                p.count = pc;
-                p.ld = pc;
-                p.xoff = p0;
-                rc = seg_scratch(c, pc, m, p);
-                if (rc) return rc;
-                if (c->time_ingest)
-                    CU(cudaEventRecord(next_event(c->ing_ev, c->ing_used, true), c->stream));
-                cudaError_t e = launch_ingest(p, c->stream);
-                if (e != cudaSuccess)
-                    return fail(c, RAD_ECUDA, "ingest launch failed: %s", cudaGetErrorString(e));
-                if (c->time_ingest)
-                    CU(cudaEventRecord(next_event(c->ing_ev, c->ing_used, false), c->stream));
-                ++c->ing_launches;
+                region = c->bstage[buf];
+                for (int sp = 0; sp < S; ++sp) {
+                    int64_t lo, cnt;
+                    range(sp, b, lo, cnt);
+                    if (cnt == 0) continue;
+                    const int64_t g0 = c->in_off[sp] + lo;
+                    p.x = region;
+                    p.u = region + m * 3 * cnt;
+                    region += 2 * m * 3 * cnt;
+                    p.step0 = t;
+                    p.n_steps = (int32_t)m;
+                    p.first = g0;
+                    p.count = cnt;
+                    p.ld = cnt;
+                    p.xoff = g0;
+                    rc = seg_scratch(c, cnt, m, p);
+                    if (rc) return rc;
+                    if (c->time_ingest)
+                        CU(cudaEventRecord(next_event(c->ing_ev, c->ing_used, true), c->stream));
+                    cudaError_t e = launch_ingest(p, c->stream);
+                    if (e != cudaSuccess)
+                        return fail(c, RAD_ECUDA, "ingest launch failed: %s", cudaGetErrorString(e));
+                    if (c->time_ingest)
+                        CU(cudaEventRecord(next_event(c->ing_ev, c->ing_used, false), c->stream));
+                    ++c->ing_launches;
+                }
                 CU(cudaEventRecord(c->used_done[buf], c->stream));
             }
             if (ev_idx >= 0) {
@@ -1248,8 +1301,7 @@ int rad_accumulate_steps(rad_ctx* c, int64_t step0, int64_t n, const double* x, 
     } else if (dx && du) {
         rc = ingest_device(c, step0, n, x, u);
         if (rc) return rc;
-    } else if (!dx && !du && c->n_species == 1 && !c->opt.defer && n >= 64 &&
-               c->n_in >= 64 * kTileP * kHostBlocks) {
+    } else if (!dx && !du && !c->opt.defer && n >= 64 && c->n_in >= 64 * kTileP * kHostBlocks) {
         rc = ingest_host_blocked(c, step0, n, x, u);
         if (rc) return rc;
     } else {

@@ -436,3 +436,25 @@ def test_batches_across_calls(precision, host):
             s += n
         got = r.finalize()
     _check(got, ref, 1e-10 if precision == 0 else 1e-4, per_direction=True)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_host_blocked_transfer_two_species(precision):
+    """Host inputs of two species (1701 electrons + 390 ions, m = 16, q = +1):
+    every block carries a share of each species; windows over electrons only,
+    ions only and both close inside the batch; a 1 MiB staging cap splits the
+    copies.  Against the device-input result and the oracle."""
+    R = _rad()
+    w = trajgen.Workload("blocked-2sp", [(1701, -1.0, 1.0, 3.0), (390, 1.0, 16.0, 3.0)], 151, 0.05,
+                         np.array([[0.0, 1.0, 0.0], [0.6, 0.0, 0.8]]),
+                         [trajgen.log_grid(0.1, 200.0, 40), np.linspace(0.5, 20.0, 23)],
+                         [(0, 150, 3, 0), (20, 110, 1, 1), (40, 150, 2, 0), (70, 90, 3, 1)],
+                         b_rms=0.3)
+    X, U = w.trajectory_numpy()
+    species = [(s[0], s[1]) for s in w.species]
+    dev = _run(w, X, U, precision)
+    host = _run(w, X, U, precision, options={"host_stage_mib": 1}, device_inputs=False)
+    for g, e in zip(host, dev):
+        np.testing.assert_allclose(g, e, rtol=1e-11, atol=1e-300)
+    ref = oracle.spectra(X, U, w.dt, w.dirs, w.grids, w.windows, species, box_L=w.L)
+    _check(host, ref, 1e-10 if precision == 0 else 1e-4, per_direction=True)
