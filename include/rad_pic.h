@@ -84,10 +84,11 @@ int64_t rad_pic_steps_done(const rad_pic *p);
 int rad_pic_tracked(rad_pic *p, int64_t first, int64_t count, double *x_out, double *u_out);
 
 /* In-situ run: n_steps times, hand the tracked particles (first .. first +
- * count - 1, the radiation context's particles in order) to rad_accumulate
- * as call s = rad_pic_steps_done() and advance one step; then hand over the
+ * count - 1, the radiation context's particles in order; count must equal
+ * the context's particle count, else RAD_PIC_EINVAL) to rad_accumulate as
+ * call s = rad_pic_steps_done() and advance one step; then hand over the
  * final state too, so every window that ends at the last step closes.  A
- * state already handed to this radiation context (the final state of a
+ * state the radiation context has already received (the final state of a
  * previous run) is not handed over twice.  Staging buffers are the PIC's. */
 int rad_pic_run_coupled(rad_pic *p, rad_ctx *r, int64_t first, int64_t count, int32_t n_steps);
 

@@ -1023,6 +1023,8 @@ static int complete_windows(rad_ctx* c, F copy)
 
 namespace rad {
 cudaStream_t ctx_stream(const rad_ctx* c) { return c ? c->stream : nullptr; }
+int64_t ctx_particles(const rad_ctx* c) { return c ? c->n_in : -1; }
+int64_t ctx_next_step(const rad_ctx* c) { return c ? c->next_step : -1; }
 }  // namespace rad
 
 extern "C" {

@@ -292,6 +292,9 @@ const void* ingest_kernel_ptr();
 // Stream a radiation context orders its work on (for in-library callers that
 // hand it device buffers from another stream).
 cudaStream_t ctx_stream(const rad_ctx* c);
+// Particles a radiation context takes per call, and the step it expects next.
+int64_t ctx_particles(const rad_ctx* c);
+int64_t ctx_next_step(const rad_ctx* c);
 // FP32 kernel variant: frequencies per thread, of which np by the FMA-pipe
 // polynomial, anchor interval K, coherent sum, minimum resident blocks per SM.
 struct Accum32Config {

@@ -282,8 +282,6 @@ struct rad_pic {
     double* ut = nullptr;
     int64_t staged = 0;
     int64_t steps = 0;
-    int64_t last_handed = -1;   // last state handed to a radiation context
-    const void* last_ctx = nullptr;
     cudaEvent_t staged_ev = nullptr;   // staging buffers written (PIC stream)
     cudaEvent_t read_ev = nullptr;     // staging buffers read (radiation stream)
     cudaStream_t st = nullptr;
@@ -452,6 +450,9 @@ int rad_pic_run_coupled(rad_pic* p, rad_ctx* r, int64_t first, int64_t count, in
 {
     if (!p || !r || n_steps < 0 || first < 0 || count < 1 || first + count > p->dev.N)
         return pfail(p, RAD_PIC_EINVAL, "rad_pic_run_coupled: bad arguments");
+    if (rad::ctx_particles(r) != count)
+        return pfail(p, RAD_PIC_EINVAL, "rad_pic_run_coupled: count differs from the radiation "
+                                        "context's particle count");
     if (p->staged < count) {
         if (p->xt) cudaFree(p->xt);
         if (p->ut) cudaFree(p->ut);
@@ -474,7 +475,8 @@ int rad_pic_run_coupled(rad_pic* p, rad_ctx* r, int64_t first, int64_t count, in
     const cudaStream_t rs = rad::ctx_stream(r);
     const bool other = rs != p->st;
     auto hand_over = [&]() -> int {
-        if (p->last_ctx == r && p->last_handed == p->steps) return RAD_PIC_OK;
+        // a state the context has already received (the final state of a previous run)
+        if (rad::ctx_next_step(r) == p->steps + 1) return RAD_PIC_OK;
         if (other) PCU(cudaStreamWaitEvent(p->st, p->read_ev, 0));
         gather_range<<<grid_for(count), 256, 0, p->st>>>(p->x, p->u, p->dev.N, first, count, p->xt,
                                                          p->ut);
@@ -486,8 +488,6 @@ int rad_pic_run_coupled(rad_pic* p, rad_ctx* r, int64_t first, int64_t count, in
         const int rc = rad_accumulate(r, p->steps, p->xt, p->ut);
         if (rc != RAD_OK) return pfail(p, RAD_PIC_ERAD, std::string("rad_accumulate: ") + rad_last_error(r));
         if (other) PCU(cudaEventRecord(p->read_ev, rs));
-        p->last_ctx = r;
-        p->last_handed = p->steps;
         return RAD_PIC_OK;
     };
     for (int32_t s = 0; s < n_steps; ++s) {

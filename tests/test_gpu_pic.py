@@ -171,6 +171,14 @@ def test_pic_rejects_bad_arguments():
             p.tracked(0, 4, np.empty((3, 4)), np.empty((3, 4)))   # host buffers
     with pytest.raises(RuntimeError):
         pic.Pic(16, 0.1, 0.1, [(1, -1.0, 1.0, 1.0)], np.zeros((3, 1)), np.zeros((3, 1)))  # Courant
+    # a coupled run must hand over exactly the radiation context's particle count
+    from paper_1003_1140_gb300 import rad as R
+    with pic.Pic.two_stream(ts) as p, \
+            R.Radiation(np.array([[0.0, 1.0, 0.0]]), [np.linspace(1.0, 2.0, 8)], ts.dt,
+                        [(16, -1.0, 1.0)], [(0, 4, 1, 0)], box_L=ts.L) as r:
+        with pytest.raises(RuntimeError):
+            p.run_coupled(r, 0, 8, 4)
+        assert p.steps_done == 0
 
 
 def test_insitu_run_small():
