@@ -35,7 +35,21 @@
  *
  * Errors: every int-returning call returns RAD_OK (0) or a negative RAD_E*
  * code; rad_last_error() gives a one-line description.  A failed call leaves
- * the context usable unless it returns RAD_ECUDA.
+ * the context usable unless it returns RAD_ECUDA.  Every device-side wait is
+ * bounded: if one expires the kernel raises an error word and returns, and
+ * rad_finalize / rad_partial_sums report RAD_ETIMEOUT (rad_reset clears it).
+ *
+ * Failure-detection test hooks: the environment variable RAD_FAULT, read by
+ * rad_init, holds comma-separated tokens (an unknown token makes rad_init
+ * return RAD_EINVAL):
+ *   alloc   rad_init fails as if an allocation had failed (RAD_ENOMEM);
+ *   graph   step-graph capture fails: the context falls back to direct
+ *           launches and rad_get_options reports use_graph = 0;
+ *   step:N  the call starting at step N is lost once (returns RAD_OK, does
+ *           nothing), so the next call returns RAD_ESTEP until N is resent;
+ *   stall   in the next directly launched accumulation kernel, block 0 waits
+ *           on a barrier nothing arrives on until the bounded wait expires,
+ *           so rad_finalize returns RAD_ETIMEOUT (once).
  */
 #ifndef RAD_H
 #define RAD_H

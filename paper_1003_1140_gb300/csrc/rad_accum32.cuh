@@ -196,6 +196,11 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
         // cur is the chunk being turned into geometry; nxt, one chunk ahead, is
         // the only cursor that advances (and so the only one that takes items
         // from the counter): each item is fetched exactly once.
+        if (p.fault_stall && blockIdx.x == 0) {
+            // test hook: buffer 1 is released only after chunk 1 has been
+            // produced, so nothing arrives during this wait and it expires
+            mbar_wait_bounded(&S.gempty[1], 0, abort_flag, p.err_word);
+        }
         ChunkCursor cur;
         cur.load_item(p, lane);
         bool pending[2] = {false, false};     // copy issued, not yet seen landed
@@ -259,9 +264,13 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                     nul[i] = p.nu_lo[kk];
                 }
             }
-            if (L >= 2) mbar_wait_bounded(&S.gempty[buf], ((L - 2) >> 1) & 1, abort_flag, p.err_word);
-            if (mbar_wait_bounded(&S.tfull[buf], (L >> 1) & 1, abort_flag, p.err_word))
-                pending[buf] = false;
+            // after an abort, produce nothing more: the compute warps may still
+            // read this buffer, and its copy may not have landed
+            if (L >= 2 &&
+                !mbar_wait_bounded(&S.gempty[buf], ((L - 2) >> 1) & 1, abort_flag, p.err_word))
+                break;
+            if (!mbar_wait_bounded(&S.tfull[buf], (L >> 1) & 1, abort_flag, p.err_word)) break;
+            pending[buf] = false;
             const int64_t c = cur.c;
             // anchor reference phase of (particle pp, block b):
             //   phi_ref = (a + K - 1) dt - n . r_a,  a = 32 c + K b   (float-float)

@@ -50,6 +50,13 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
 
     if (warp == kComputeWarps) {
         if (lane != 0) return;
+        if (p.fault_stall && blockIdx.x == 0) {
+            // test hook: buffer 1 is released only after its first chunk has
+            // been issued, so nothing arrives during this wait and it expires
+            mbar_wait_bounded(&S.empty[1], 0, abort_flag, p.err_word);
+        }
+        bool pending[2] = {false, false};   // a copy was issued into the buffer
+        uint32_t pend_parity[2] = {0, 0};   // phase parity of its latest copy
         uint32_t L = 0;
         for (int ii = blockIdx.x; ii < p.n_items; ii += gridDim.x) {
             const WorkItem it = p.items[ii];
@@ -63,6 +70,8 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
                     if (L >= 2) mbar_wait_bounded(&S.empty[buf], ((L - 2) >> 1) & 1, abort_flag,
                                                   p.err_word);
                     if (*abort_flag) continue;
+                    pending[buf] = true;
+                    pend_parity[buf] = (L >> 1) & 1;
                     mbar_arrive_expect_tx(&S.full[buf], kBytes);
                     const int64_t slot = (c * kChunk64) % p.ring;
                     const double* src = p.slab64 + (tile * p.ring + slot) * (kComps * kTileP);
@@ -70,10 +79,10 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
                 }
             }
         }
-        if (L >= 1) mbar_wait_bounded(&S.full[(L - 1) & 1], ((L - 1) >> 1) & 1, abort_flag,
-                                      p.err_word);
-        if (L >= 2) mbar_wait_bounded(&S.full[(L - 2) & 1], ((L - 2) >> 1) & 1, abort_flag,
-                                      p.err_word);
+        // never leave the block with a copy in flight, also after an abort
+        // (bounded; the latest copy into a buffer is the last phase it completes)
+        for (int b = 0; b < 2; ++b)
+            if (pending[b]) mbar_drain(&S.full[b], pend_parity[b]);
         return;
     }
 

@@ -39,6 +39,54 @@ struct StepGraph {
     cudaGraphNode_t ingest_node = nullptr;
 };
 
+// Failure-detection test hooks, read from the RAD_FAULT environment variable
+// at rad_init (comma-separated tokens; unset or empty: none).  Every failure
+// they cause is made on the host or by a bounded device wait:
+//   alloc   rad_init fails as if the ring allocation had failed (RAD_ENOMEM)
+//           after the tables are allocated, so the cleanup path runs;
+//   graph   step-graph capture fails: the context falls back to direct
+//           launches (rad_get_options then reports use_graph = 0);
+//   step:N  the call starting at step N is lost once (it returns RAD_OK and
+//           does nothing); the next call is refused with RAD_ESTEP and the
+//           caller can hand step N over again;
+//   stall   the next directly launched accumulation kernel holds block 0's
+//           producer in a wait nothing ends, until the bounded wait expires:
+//           the device error word is raised and rad_finalize returns
+//           RAD_ETIMEOUT (once; rad_reset clears the error).
+struct FaultHooks {
+    bool alloc = false, graph = false, stall = false;
+    int64_t drop_step = -1;
+};
+
+static bool parse_fault_env(FaultHooks& f)
+{
+    const char* env = std::getenv("RAD_FAULT");
+    if (!env) return true;
+    std::stringstream ss(env);
+    std::string tok;
+    while (std::getline(ss, tok, ',')) {
+        if (tok.empty()) continue;
+        if (tok == "alloc") {
+            f.alloc = true;
+        } else if (tok == "graph") {
+            f.graph = true;
+        } else if (tok == "stall") {
+            f.stall = true;
+        } else if (tok.compare(0, 5, "step:") == 0) {
+            char* end = nullptr;
+            const long long v = std::strtoll(tok.c_str() + 5, &end, 10);
+            if (end == tok.c_str() + 5 || *end != '\0' || v < 0) return false;
+            f.drop_step = v;
+        } else {
+            return false;
+        }
+    }
+    return true;
+}
+
+// Internal status of graph_for: capture was not possible, launch directly.
+constexpr int kGraphUnavailable = 1;
+
 struct rad_ctx {
     // configuration
     int D = 0;
@@ -128,6 +176,9 @@ struct rad_ctx {
     // plain step, 1 + e the step that closes event e
     std::vector<StepGraph> graphs;
     cudaStream_t cap_stream = nullptr;
+    bool graph_off = false;        // capture failed once: direct launches only
+
+    FaultHooks fault;
 
     std::string err;
 };
@@ -550,6 +601,14 @@ static int freeze(rad_ctx* c)
     return RAD_OK;
 }
 
+// The stall hook applies to one launch only.
+static int32_t take_stall(rad_ctx* c)
+{
+    const bool s = c->fault.stall;
+    c->fault.stall = false;
+    return s ? 1 : 0;
+}
+
 static int launch_event(rad_ctx* c, Event& ev)
 {
     if (ev.items.empty()) return RAD_OK;
@@ -571,6 +630,7 @@ static int launch_event(rad_ctx* c, Event& ev)
         p.dt = c->dt / c->nsub;
         p.acc = c->acc;
         p.err_word = c->d_err;
+        p.fault_stall = take_stall(c);
         e = launch_accum64(p, c->mode == RAD_COHERENT, grid, c->stream);
     } else {
         Accum32Params p{};
@@ -591,6 +651,7 @@ static int launch_event(rad_ctx* c, Event& ev)
         p.dt_lo = (float)(c->dt / c->nsub - (double)p.dt_hi);
         p.acc = c->acc;
         p.err_word = c->d_err;
+        p.fault_stall = take_stall(c);
         CU(cudaMemsetAsync(c->d_counter, 0, sizeof(int), c->stream));
         e = cudaSuccess;
         if (!accum32_dispatch(&p, c->cfg, grid, c->stream, &e, nullptr))
@@ -902,6 +963,8 @@ static int graph_for(rad_ctx* c, int kind, const IngestParams& ip, StepGraph** o
     if ((int)c->graphs.size() < 1 + (int)c->events.size()) c->graphs.resize(1 + c->events.size());
     StepGraph& g = c->graphs[kind];
     if (!g.exec) {
+        if (c->fault.graph)
+            return fail(c, kGraphUnavailable, "step graph capture failed (RAD_FAULT=graph)");
         if (!c->cap_stream) CU(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
         CU(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = launch_ingest(ip, c->cap_stream);
@@ -934,9 +997,12 @@ static int graph_for(rad_ctx* c, int kind, const IngestParams& ip, StepGraph** o
         }
         cudaGraph_t graph = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
-        if (e != cudaSuccess || e2 != cudaSuccess)
-            return fail(c, RAD_ECUDA, "step graph capture failed: %s",
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();   // capture errors are not sticky: clear the last error
+            return fail(c, kGraphUnavailable, "step graph capture failed: %s",
                         cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
         g.graph = graph;
         size_t n = 0;
         CU(cudaGraphGetNodes(graph, nullptr, &n));
@@ -1048,6 +1114,7 @@ int rad_init(rad_ctx** out, const double* dirs, int32_t D, const double* freqs,
         rad_destroy(c);
         return rc;
     };
+    if (!parse_fault_env(c->fault)) return bail(RAD_EINVAL);
     c->D = D;
     c->n_grids = n_grids;
     c->dt = dt;
@@ -1175,6 +1242,7 @@ int rad_init(rad_ctx** out, const double* dirs, int32_t D, const double* freqs,
     CUB(cudaMemcpy(c->d_species, sd.data(), n_species * sizeof(SpeciesDev), cudaMemcpyHostToDevice));
 
     // ring and state
+    if (c->fault.alloc) return bail(RAD_ENOMEM);
     const int64_t nc = c->ncols;
     if (precision == RAD_FP64) {
         CUB(cudaMalloc(&c->slab64, (size_t)c->ring * kComps * nc * sizeof(double)));
@@ -1275,6 +1343,7 @@ int rad_get_options(const rad_ctx* c, rad_options* o)
 {
     if (!c || !o) return RAD_EINVAL;
     *o = c->opt;
+    if (c->graph_off) o->use_graph = 0;
     if (c->frozen && c->precision == RAD_FP32_SPLIT) {
         o->anchor_K = c->cfg.K;
         o->freq_per_lane = c->cfg.ft;
@@ -1293,12 +1362,21 @@ int rad_accumulate_steps(rad_ctx* c, int64_t step0, int64_t n, const double* x, 
         return fail(c, RAD_ESTEP, "step %lld given, %lld expected", (long long)step0,
                     (long long)c->next_step);
     if (n == 0) return RAD_OK;
+    if (c->fault.drop_step == step0) {   // test hook: this hand-over is lost once
+        c->fault.drop_step = -1;
+        return RAD_OK;
+    }
     int rc = freeze(c);
     if (rc) return rc;
     CU(cudaSetDevice(c->device));
     const bool dx = is_device_ptr(x), du = is_device_ptr(u);
-    if (dx && du && n == 1 && c->opt.use_graph && c->precision == RAD_FP32_SPLIT) {
+    if (dx && du && n == 1 && c->opt.use_graph && !c->graph_off &&
+        c->precision == RAD_FP32_SPLIT) {
         rc = step_via_graph(c, step0, x, u);
+        if (rc == kGraphUnavailable) {
+            c->graph_off = true;   // direct launches from now on
+            rc = ingest_device(c, step0, n, x, u);
+        }
         if (rc) return rc;
     } else if (dx && du) {
         rc = ingest_device(c, step0, n, x, u);

@@ -270,6 +270,9 @@ struct Accum32Params {
     float dt_hi, dt_lo;       // dt as a float-float pair
     double* acc;              // incoherent [n_out]; coherent [n_out][4]
     int* err_word;
+    // failure-detection test hook (0: off): block 0's producer first waits on
+    // a barrier nothing arrives on, so that its bounded wait expires
+    int32_t fault_stall;
 };
 
 struct Accum64Params {
@@ -284,6 +287,7 @@ struct Accum64Params {
     double dt;
     double* acc;
     int* err_word;
+    int32_t fault_stall;      // as in Accum32Params
 };
 
 cudaError_t launch_ingest(const IngestParams& p, cudaStream_t st);

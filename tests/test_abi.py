@@ -65,6 +65,27 @@ def test_rad_init_rejects_null_out_pointer():
                         0, 0, ctypes.c_double(0.0), None) == -1
 
 
+def test_fault_hook_tokens_are_checked_before_any_device_call(monkeypatch):
+    """RAD_FAULT is parsed at rad_init before the device is touched: an unknown
+    token or a malformed step number is RAD_EINVAL on any machine."""
+    import numpy as np
+    from paper_1003_1140_gb300 import rad as R
+    args = (np.array([[0.0, 1.0, 0.0]]), [np.linspace(1.0, 2.0, 4)], 0.1, [(8, -1.0)],
+            [(0, 4, 1, 0)])
+    for bad in ("explode", "stall,step:", "step:-2", "step:3x", "alloc, graph"):
+        monkeypatch.setenv("RAD_FAULT", bad)
+        with pytest.raises(R.RadError) as ei:
+            R.Radiation(*args)
+        assert ei.value.code == -1, bad
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        # accepted tokens get past the parse and stop at the device query
+        monkeypatch.setenv("RAD_FAULT", "alloc,graph,stall,step:3,")
+        with pytest.raises(R.RadError) as ei:
+            R.Radiation(*args)
+        assert ei.value.code == -3
+
+
 def test_trajectory_pusher_builds():
     pytest.importorskip("torch")
     from trajgen import gpu
