@@ -40,8 +40,8 @@ METRIC = "G particle·step·ω·n updates/s, FP32 split vs FP64 GPU at ≤1e-4 r
 # in profiles/accum32_workload2_4096p.md (4096 particles, this workload's samples,
 # directions and omegas), valid while the kernel source and its work-list builder are
 # the ones that were captured; traffic scales with the particle count.
-TRAFFIC_CAPTURE = {"sources_sha256": "5fd3d6e19e08668390f9592187cdc6d6405cf55740d414f7e3afc4eeae537b75",
-                   "bytes_per_launch": 780.564224e6, "particles": 4096}
+TRAFFIC_CAPTURE = {"sources_sha256": "423be64ff3493848bac2ae2e94d7a22be344fce6ef4372fddc847ef6273d73a6",
+                   "bytes_per_launch": 771.210496e6, "particles": 4096}
 UNIT = "G updates/s"
 WORKLOAD = 2
 

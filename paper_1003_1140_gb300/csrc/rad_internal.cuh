@@ -148,12 +148,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait: spins with a growing back-off for at most ~2^22 polls
-// (about a second).  On expiry it raises the block's abort flag and the
-// device error word, and returns false; callers then carry on without
-// waiting (results are flagged invalid) so that no thread is left behind at
-// a barrier.
-constexpr uint32_t kMaxPolls = 1u << 22;
+// Bounded wait: spins with a growing back-off for at most 2^18 polls.  A
+// poll that fails costs about 4 us on GB300 (the try_wait's own suspension
+// plus the back-off; 2^22 polls measured 17 s), so a wait expires after
+// about a second, while every wait of a working kernel ends within
+// microseconds.  On expiry it raises the block's abort flag and the device
+// error word, and returns false; callers then carry on without waiting
+// (results are flagged invalid) so that no thread is left behind at a barrier.
+constexpr uint32_t kMaxPolls = 1u << 18;
 
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
                                                   volatile int* s_abort, int* err_word)
@@ -176,8 +178,8 @@ __device__ __forceinline__ void fence_proxy_async()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// Bounded wait used only to drain copies still in flight after an abort: it
-// polls at most ~2^22 times and never raises flags.
+// Bounded wait for a block's own copies still in flight before it exits: it
+// polls at most kMaxPolls times and never raises flags.
 __device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity)
 {
     for (uint32_t it = 0; it < kMaxPolls; ++it) {

@@ -5,7 +5,6 @@ accumulation kernel's producer in block 0 waits on a barrier no one arrives
 on).  No GPU is faulted or hung: the wait expires after its poll limit, the
 kernel raises the device error word and returns, the host reports
 RAD_ETIMEOUT, and after rad_reset the same context gives the oracle's result."""
-import math
 import time
 
 import numpy as np
@@ -143,7 +142,7 @@ def test_expired_device_wait_is_reported_and_recoverable(small, monkeypatch, pre
         assert ei.value.code == RAD_ETIMEOUT
         assert "expired" in str(ei.value)
         print(f"bounded wait expired after {waited:.2f} s")
-        assert waited < 120.0
+        assert waited < 10.0         # the poll limit is about a second
         # the device is fine: an unrelated kernel runs and synchronises
         z = torch.arange(1000, device="cuda", dtype=torch.float64).sum().item()
         assert z == 999 * 1000 / 2
