@@ -322,7 +322,8 @@ int rad_pic_init(rad_pic** out, int32_t n, double d, double dt, const rad_pic_sp
 {
     if (!out) return RAD_PIC_EINVAL;
     *out = nullptr;
-    if (n < 4 || n > 16384 || !(d > 0.0) || !(dt > 0.0) || !(dt < d / std::sqrt(2.0)) ||
+    if (n < 4 || n > 16384 || !(d > 0.0) || !(dt > 0.0) || !std::isfinite(d) ||
+        !std::isfinite(dt) || !(dt < d / std::sqrt(2.0)) ||
         n_species < 0 || n_species > kMaxSpecies || (n_species > 0 && !sp))
         return RAD_PIC_EINVAL;
     int64_t N = 0;
