@@ -273,6 +273,8 @@ void rad_destroy(rad_ctx *ctx);
  *   N        : particles (>= 1); n_calls >= 2 steps of leapfrog states.
  *   x, u     : device [n_calls][3][N] FP64, x_s and u_{s-1/2} per step.
  *   spectrum : device [D][F] FP64, written by the call (the caller owns it).
+ *   (x, u and spectrum in device memory of the current device, or managed
+ *   memory; anything else is RAD_EINVAL.)
  *   cuda_stream : stream to run on (NULL: the legacy default stream).
  * Limit: the trajectory ring, anchor ring, per-particle state and
  * accumulators must fit in the 96 MiB array -- about

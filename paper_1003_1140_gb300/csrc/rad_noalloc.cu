@@ -60,6 +60,18 @@ __global__ void noalloc_finalize(const double* acc, double* out, int64_t n, int 
     }
 }
 
+// Device (or managed) memory that kernels on device dev may dereference; host
+// memory is refused before any launch instead of faulting inside one.
+bool device_memory(const void* p, int dev)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == dev);
+}
+
 // Bump allocator over the scratch array (256-byte aligned pieces).
 struct Carve {
     size_t off = 0;
@@ -102,6 +114,8 @@ extern "C" int rad_spectrum_noalloc(const double* dirs, int32_t D, const double*
     cudaDeviceProp prop;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
         return RAD_ECUDA;
+    if (!device_memory(x, dev) || !device_memory(u, dev) || !device_memory(spectrum, dev))
+        return RAD_EINVAL;
     int nb = 0;
     cudaError_t e = cudaSuccess;
     if (!accum32_dispatch(nullptr, cfg, 0, nullptr, &e, &nb) || nb < 1) return RAD_ECUDA;
