@@ -82,7 +82,8 @@ int rad_mlp_adam(rad_mlp *m, float lr, float beta1, float beta2, float eps);
  * transposed into scratch).  M, N multiples of 128, K of 64.  Default stream;
  * returns once the work is enqueued.  Products with few 128 x 128 output tiles
  * and a long K are split over K.  Scratch comes from the default stream's
- * stream-ordered pool (RAD_MLP_ENOMEM when it cannot be had). */
+ * stream-ordered pool (RAD_MLP_ENOMEM when it cannot be had).  A, B or C
+ * outside device or managed memory: RAD_MLP_EINVAL, nothing launched. */
 int rad_mlp_gemm(int32_t a_kcontig, int32_t b_kcontig, int32_t M, int32_t N, int32_t K,
                  const void *A, const void *B, float *C);
 

@@ -983,6 +983,10 @@ int rad_mlp_gemm(int32_t a_kcontig, int32_t b_kcontig, int32_t M, int32_t N, int
 {
     if (M < 1 || N < 1 || K < 1 || M % BM || N % BN || K % BK || !A || !B || !C)
         return fail(RAD_MLP_EINVAL, "rad_mlp_gemm: M, N must be multiples of 128 and K of 64");
+    // the kernels load A and B by TMA and write C directly: host memory is
+    // refused here instead of faulting inside a launch
+    if (!is_dev(A) || !is_dev(B) || !is_dev(C))
+        return fail(RAD_MLP_EINVAL, "rad_mlp_gemm: A, B and C must be device or managed memory");
     int* err = gemm_err_word();
     if (!err) return fail(RAD_MLP_ECUDA, "rad_mlp_gemm: error word");
     Epilogue ep{nullptr, nullptr, C, nullptr, 0};
