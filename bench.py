@@ -24,6 +24,7 @@ import argparse
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -38,9 +39,9 @@ METRIC = "G particle·step·ω·n updates/s, FP32 split vs FP64 GPU at ≤1e-4 r
 
 # DRAM bytes (read + write) of one accumulation launch, from the ncu capture summarised
 # in profiles/accum32_workload2_4096p.md (4096 particles, this workload's samples,
-# directions and omegas), valid while the kernel source and its work-list builder are
-# the ones that were captured; traffic scales with the particle count.
-TRAFFIC_CAPTURE = {"sources_sha256": "423be64ff3493848bac2ae2e94d7a22be344fce6ef4372fddc847ef6273d73a6",
+# directions and omegas), valid while the code (comments aside) of the kernel and of its
+# work-list builder is the code that was captured; traffic scales with the particle count.
+TRAFFIC_CAPTURE = {"sources_sha256": "dfb57359011610ba530d66841db0796ff7922217d90d7ca8ac14fab739b638f4",
                    "bytes_per_launch": 771.210496e6, "particles": 4096}
 UNIT = "G updates/s"
 WORKLOAD = 2
@@ -134,15 +135,31 @@ def run_reference(args):
     return 0
 
 
-def captured_traffic(n_particles: int):
-    """DRAM bytes per accumulation launch from the ncu capture, or None if the kernel
-    or its work-list builder changed since the capture."""
+_C_TOKENS = re.compile(r'"(?:\\.|[^"\\])*"|\'(?:\\.|[^\'\\])*\'|//[^\n]*|/\*.*?\*/', re.S)
+
+
+def code_only(src: str) -> str:
+    """C/C++/CUDA source with its comments removed and whitespace runs collapsed:
+    the text the compiler acts on, so that editing a comment does not void a capture."""
+    return " ".join(_C_TOKENS.sub(lambda m: " " if m.group(0)[0] == "/" else m.group(0),
+                                  src).split())
+
+
+def traffic_sources_hash() -> str:
+    """SHA-256 over the code (not the comments) of the accumulation kernel and of
+    the host library that builds its work list and launches it."""
     import hashlib
     h = hashlib.sha256()
     for f in ("paper_1003_1140_gb300/csrc/rad_accum32.cuh", "paper_1003_1140_gb300/csrc/rad_api.cu"):
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
-    if h.hexdigest() != TRAFFIC_CAPTURE["sources_sha256"]:
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            h.update(code_only(fh.read()).encode())
+    return h.hexdigest()
+
+
+def captured_traffic(n_particles: int):
+    """DRAM bytes per accumulation launch from the ncu capture, or None if the code
+    of the kernel or of its work-list builder changed since the capture."""
+    if traffic_sources_hash() != TRAFFIC_CAPTURE["sources_sha256"]:
         return None
     return TRAFFIC_CAPTURE["bytes_per_launch"] * n_particles / TRAFFIC_CAPTURE["particles"]
 

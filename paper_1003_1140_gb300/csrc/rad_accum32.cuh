@@ -31,7 +31,7 @@
 //   sin (degree 9) and cos (degree 8) on [-pi/2, pi/2], double angle -- so
 //   both the MUFU and the FMA pipes carry the transcendental work.
 // * The trajectory ring is tile-major ([tile][slot][comp][8 particles]), so a
-//   chunk of 32 samples x 10 components x 8 particles is one contiguous 10 KB
+//   chunk of 32 samples x 11 components x 8 particles is one contiguous 11 KB
 //   block (its anchor positions another), staged into shared memory by bulk
 //   TMA copies (cp.async.bulk).  Warp specialisation: a producer warp issues
 //   the copies and turns each chunk into geometry and anchor phases in shared

@@ -5,8 +5,8 @@
 // ring's absolute FP64 positions, theta = w_k phi_m, e^{i theta} by CUDA's
 // double-precision sincos, FP64 accumulators and FP64 particle sums.  This is
 // the GPU reference against which the FP32 split path is judged; on GB300 it
-// is bound by the FP64 pipe.  Trajectory chunks (16 samples x 10 components
-// x 8 particles, FP64; one contiguous 10 KB block of the tile-major ring) are
+// is bound by the FP64 pipe.  Trajectory chunks (16 samples x 11 components
+// x 8 particles, FP64; one contiguous 11 KB block of the tile-major ring) are
 // staged by bulk TMA copies exactly as in the FP32 path.
 #include "rad_internal.cuh"
 

@@ -45,3 +45,13 @@ def test_reference_arm_other_ranks_exit_quietly():
                env={"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_traffic_hash_ignores_comments_but_not_code():
+    sys.path.insert(0, ROOT)
+    import bench
+    src = 'int a = b / c; // note\n/* block\n comment */ const char* s = "// kept /* kept */";\n'
+    assert bench.code_only(src) == 'int a = b / c; const char* s = "// kept /* kept */";'
+    assert bench.code_only("x = 1; // one") == bench.code_only("x  =  1;\n/* other */")
+    assert bench.code_only("x = 1;") != bench.code_only("x = 2;")
+    assert bench.code_only("c = '/'; d = '*';") == "c = '/'; d = '*';"
