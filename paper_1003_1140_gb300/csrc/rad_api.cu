@@ -2,9 +2,9 @@
 //
 // Owns the context: observer basis, frequency tables, species/column map,
 // the trajectory ring and per-particle leapfrog state, the FP64 spectrum
-// accumulators, the per-event work lists and the TMA descriptors.  Every
-// arithmetic step of the diagnostic runs in the kernels of rad_ingest.cu,
-// rad_accum32.cu, rad_accum64.cu and the finalize kernel below.
+// accumulators and the per-event work lists.  Every arithmetic step of the
+// diagnostic runs in the kernels of rad_ingest.cu, rad_accum32.cuh (built in
+// rad_accum32_ft*.cu), rad_accum64.cu and the finalize kernel below.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -266,10 +266,10 @@ static int freq_tile(const rad_ctx* c)
     return c->precision == RAD_FP64 ? 32 * accum64_ft() : 32 * c->cfg.ft;
 }
 
-// Build the work items of one event (set of windows) and sort by cost.
-// Work items of an event's windows; with `ranges` only the particle tiles
-// [first, second) of each species (the blocked host path), the groups sized for
-// those tiles so that every list balances over the GPU.
+// Build the work items of one event (set of windows) and sort them by cost;
+// with `ranges` only the particle tiles [first, second) of each species (the
+// blocked host path), the groups sized for those tiles so that every list
+// balances over the GPU.
 static void build_items(rad_ctx* c, Event& ev, int total_blocks,
                         const std::vector<std::pair<int, int>>* ranges = nullptr)
 {
@@ -509,7 +509,7 @@ static int autotune32(rad_ctx* c, int K)
     return RAD_OK;
 }
 
-// Freeze options: pick K / FT, build events, item lists, TMA map.
+// Freeze options: pick K / FT, build events and their item lists.
 static int freeze(rad_ctx* c)
 {
     if (c->frozen) return RAD_OK;
@@ -757,7 +757,7 @@ static int ingest_device(rad_ctx* c, int64_t step0, int64_t n, const double* x, 
     return RAD_OK;
 }
 
-// Host inputs, one species, eager windows: the particle axis is cut into a few
+// Host inputs, eager windows: the particle axis is cut into a few
 // blocks of whole tiles.  Each block's share of the call's steps is copied
 // (pitched copies on the copy stream, double-buffered) and ingested on its own,
 // and at every window close only that block's work items are launched.  The
