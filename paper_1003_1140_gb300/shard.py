@@ -10,6 +10,7 @@ data path -- only this final reduction.
 from __future__ import annotations
 
 import math
+import time
 
 import numpy as np
 
@@ -37,11 +38,42 @@ def combine(partials, coherent: bool):
     return spectrum_from_sums(total, coherent)
 
 
-def allreduce_spectrum(partial, coherent: bool, group=None):
+def check_in(store, rank: int, tag: str) -> None:
+    """Record in a key-value store (a torch.distributed Store) that this rank's
+    shard is done for `tag` (a window, a batch of steps)."""
+    store.set(f"{tag}/done/{int(rank)}", "1")
+
+
+def missing_ranks(store, world: int, tag: str, timeout_s: float) -> list:
+    """Ranks that have not checked in for `tag` within timeout_s seconds (empty
+    when every rank has).  Polls the store; never enters a collective."""
+    deadline = time.monotonic() + float(timeout_s)
+    missing = list(range(int(world)))
+    while True:
+        missing = [r for r in missing if not store.check([f"{tag}/done/{r}"])]
+        if not missing or time.monotonic() >= deadline:
+            return missing
+        time.sleep(0.02)
+
+
+def allreduce_spectrum(partial, coherent: bool, group=None, store=None, tag: str = "",
+                       timeout_s: float = 30.0):
     """Sum the partials over the torch.distributed group (gloo or nccl) and return
-    the spectrum of all ranks' particles on every rank."""
+    the spectrum of all ranks' particles on every rank.
+
+    With a store, every rank first checks in for `tag` and waits (up to
+    timeout_s) for the others: a rank that failed or left before finishing its
+    shard is reported as a RuntimeError naming it, before any rank enters the
+    collective, instead of leaving the others blocked in it."""
     import torch
     import torch.distributed as dist
+    if store is not None:
+        world = dist.get_world_size(group)
+        check_in(store, dist.get_rank(group), tag)
+        missing = missing_ranks(store, world, tag, timeout_s)
+        if missing:
+            raise RuntimeError(f"ranks {missing} did not finish their shard of {tag!r} "
+                               f"within {timeout_s:g} s")
     t = torch.as_tensor(np.ascontiguousarray(partial, dtype=np.float64))
     if dist.is_initialized() and dist.get_backend(group) == "nccl":
         t = t.cuda()

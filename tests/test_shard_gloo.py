@@ -87,3 +87,80 @@ def test_shard_ranges_cover_and_balance():
             for (f0, n0), (f1, _) in zip(rs, rs[1:]):
                 assert f0 + n0 == f1
             assert max(n for _, n in rs) - min(n for _, n in rs) <= 1
+
+
+# ---------------------------------------------------------------------------
+# failure detection between ranks, on the host (no GPU is involved)
+# ---------------------------------------------------------------------------
+def _failure_worker(rank, world, port, store_port, mode, result_q):
+    """mode "ok": both ranks check in and reduce; "fail": rank 1 raises before it
+    checks in (its shard failed); "leave": rank 1 exits right after joining and
+    rank 0 reduces without a store (only the process-group timeout can end it)."""
+    import datetime
+    import time as _time
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=5))
+    store = dist.TCPStore("127.0.0.1", store_port, world, is_master=(rank == 0),
+                          timeout=datetime.timedelta(seconds=30), wait_for_workers=False)
+    from paper_1003_1140_gb300 import shard
+    part = np.full(6, float(rank + 1))
+    if rank == 1 and mode == "leave":
+        os._exit(0)                                  # gone between steps, nothing in flight
+    if rank == 1 and mode == "fail":
+        raise RuntimeError("shard 1 failed")         # never checks in
+    t0 = _time.monotonic()
+    try:
+        if mode == "leave":
+            S = shard.allreduce_spectrum(part, False)
+        else:
+            S = shard.allreduce_spectrum(part, False, store=store, tag="window-0", timeout_s=2.0)
+        out = ("ok", S.tolist(), _time.monotonic() - t0)
+    except Exception as e:                           # noqa: BLE001 -- reported to the test
+        out = ("raised", str(e), _time.monotonic() - t0)
+    if rank == 0:
+        result_q.put(out)
+        result_q.close()
+        result_q.join_thread()                       # flush before the hard exit
+    if mode == "ok":
+        dist.destroy_process_group()
+    os._exit(0)
+
+
+def _run_failure_case(mode):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port, store_port = _free_port(), _free_port()
+    procs = [ctx.Process(target=_failure_worker, args=(r, 2, port, store_port, mode, q))
+             for r in range(2)]
+    for p in procs:
+        p.start()
+    try:
+        return q.get(timeout=120)
+    finally:
+        for p in procs:
+            p.join(timeout=30)
+            if p.is_alive():
+                p.kill()                              # this test's own child, by handle
+                p.join(timeout=10)
+
+
+def test_check_in_then_reduce():
+    kind, S, _ = _run_failure_case("ok")
+    assert kind == "ok"
+    np.testing.assert_allclose(S, 3.0 / (4 * math.pi ** 2))  # 1 + 2 over both ranks
+
+
+def test_a_rank_that_failed_is_named_before_the_reduction():
+    kind, msg, waited = _run_failure_case("fail")
+    assert kind == "raised" and "[1]" in msg and "window-0" in msg
+    assert waited < 10.0
+
+
+def test_a_reduction_whose_peer_left_ends_with_an_error():
+    kind, msg, waited = _run_failure_case("leave")
+    assert kind == "raised"
+    assert waited < 60.0
