@@ -29,7 +29,7 @@ the oracle hands both the same generated arrays.
 from __future__ import annotations
 
 import math
-from dataclasses import dataclass, field as dc_field
+from dataclasses import dataclass
 
 import numpy as np
 
