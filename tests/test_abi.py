@@ -90,3 +90,46 @@ def test_trajectory_pusher_builds():
     pytest.importorskip("torch")
     from trajgen import gpu
     assert os.path.exists(gpu.build())
+
+
+def test_headers_are_plain_c_and_every_symbol_links(tmp_path):
+    """A C program (C99, -pedantic -Werror) that includes all three headers and takes
+    the address of every declared function links against the library; running it
+    calls only entry points that reject their arguments before touching a device."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no gcc")
+    from paper_1003_1140_gb300 import build
+    lib = build.build()
+    names = sorted(set(declared_symbols("rad.h") + declared_symbols("rad_mlp.h")
+                       + declared_symbols("rad_pic.h")))
+    src = tmp_path / "abi.c"
+    src.write_text(
+        "#include <stddef.h>\n#include <stdio.h>\n"
+        '#include "rad.h"\n#include "rad_mlp.h"\n#include "rad_pic.h"\n'
+        "typedef void (*fn)(void);\n"
+        "static const fn every[] = {\n" + ",\n".join(f"    (fn){n}" for n in names) + "\n};\n"
+        "int main(void) {\n"
+        "    rad_options o = {0};\n"
+        "    int bad = 0;\n"
+        "    (void)o;\n"
+        "    bad |= rad_init(NULL, NULL, 0, NULL, NULL, 0, 0.0, NULL, 0, NULL, 0, 0, 0, 0.0,\n"
+        "                    NULL) != RAD_EINVAL;\n"
+        "    bad |= rad_pic_init(NULL, 0, 0.0, 0.0, NULL, 0, NULL, NULL, NULL) != RAD_PIC_EINVAL;\n"
+        "    bad |= rad_mlp_init(NULL, NULL, 0, 0, NULL) != RAD_MLP_EINVAL;\n"
+        "    bad |= rad_spectrum_size(NULL) != -1;\n"
+        "    printf(\"%d symbols\\n\", (int)(sizeof every / sizeof every[0]));\n"
+        "    return bad;\n"
+        "}\n")
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(lib)
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                        "-L", libdir, "-l:" + os.path.basename(lib), "-Wl,-rpath," + libdir],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.strip() == f"{len(names)} symbols"
