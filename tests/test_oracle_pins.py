@@ -500,6 +500,80 @@ def test_subsamples_reduce_to_textbook_cases():
     np.testing.assert_allclose(bd[:, 0, 0], 0.5 / (1 + ut ** 2) ** 1.5, rtol=1e-13)
 
 
+def _constant_force_history(ux0, uy, a, dt, nc):
+    """Leapfrog states of u(t) = (ux0 + a t, uy, 0) (a constant force along x on a
+    particle that also moves along y, so beta turns), with the exact positions
+    x(t) = int beta dt: gamma = sqrt(1 + u^2) changes as dgamma/dt = a u_x / gamma, so
+    r_x(t) = (gamma(t) - gamma(0)) / a and
+    r_y(t) = (u_y / a) (asinh(u_x(t) / c) - asinh(u_x(0) / c)), c = sqrt(1 + u_y^2)."""
+    c = math.sqrt(1.0 + uy * uy)
+
+    def ux(t):
+        return ux0 + a * t
+
+    def pos(t):
+        g = np.sqrt(1.0 + ux(t) ** 2 + uy * uy)
+        g0 = math.sqrt(1.0 + ux0 * ux0 + uy * uy)
+        return np.stack([(g - g0) / a, (uy / a) * (np.arcsinh(ux(t) / c) - math.asinh(ux0 / c)),
+                         np.zeros_like(g)])
+
+    s = np.arange(nc) * dt
+    X = pos(s).T[:, :, None].copy()                       # x_s at t = s dt
+    U = np.zeros((nc, 3, 1))
+    U[:, 0, 0] = ux(s - 0.5 * dt)                          # u_{s-1/2}
+    U[:, 1, 0] = uy
+    return X, U, pos
+
+
+@pytest.mark.parametrize("uy", [0.0, 1.3])
+def test_subsample_positions_follow_the_exact_path(uy):
+    """Sec. 2.2 sub-cycling: with u exactly linear in time the sub-sample positions
+    must be the exact path integral r(t) = r_m + int_{t_m}^{t} beta dt' at every
+    sub-sample time (m + tau_k) dt.  Simpson's rule over a step of |tau| dt <= dt / 2
+    is exact to h^5 max|beta''''| / 2880 ~ 1e-11 here, so a 1e-10 bound fails for a
+    trapezoid rule (error ~ h^3 beta'' ~ 1e-5), for beta(tau / 2) taken at tau, or
+    for a wrong sub-sample time."""
+    dt, nc, n, a = 0.1, 7, 5, 0.5
+    X, U, pos = _constant_force_history(-0.4, uy, a, dt, nc)
+    r, b, bd = oracle.subsamples(X, U, dt, 0.0, n)
+    tau = (np.arange(n) + 0.5) / n - 0.5
+    t = ((np.arange(nc - 1)[:, None] + tau[None, :]) * dt).reshape(-1)
+    exact = pos(t).T
+    np.testing.assert_allclose(r[:, :, 0], exact, rtol=0, atol=1e-10)
+    # beta and betadot of the same path (u = u(t), betadot = d(u/gamma)/dt)
+    u = np.stack([-0.4 + a * t, np.full_like(t, uy), np.zeros_like(t)], 1)
+    g = np.sqrt(1.0 + (u * u).sum(1, keepdims=True))
+    np.testing.assert_allclose(b[:, :, 0], u / g, rtol=0, atol=1e-14)
+    udot = np.array([a, 0.0, 0.0])
+    bdot = udot / g - u * (u @ udot)[:, None] / g ** 3
+    np.testing.assert_allclose(bd[:, :, 0], bdot, rtol=0, atol=1e-13)
+
+
+def test_subsample_position_pin_catches_a_trapezoid_rule():
+    """The 1e-10 bound above is tight enough: the same sub-sample positions by a
+    trapezoid rule over [0, tau] (weights 1/2, 1/2), or by Simpson's rule with the
+    midpoint velocity taken at the end point, miss the exact path by far more."""
+    dt, nc, n, a, uy = 0.1, 7, 5, 0.5, 1.3
+    X, U, pos = _constant_force_history(-0.4, uy, a, dt, nc)
+    r, _, _ = oracle.samples(X, U, dt, 0.0)
+    tau = (np.arange(n) + 0.5) / n - 0.5
+    ub = 0.5 * (U[:-1] + U[1:])
+    du = U[1:] - U[:-1]
+
+    def beta(uu):
+        return uu / np.sqrt(1.0 + (uu * uu).sum(1, keepdims=True))
+
+    t = ((np.arange(nc - 1)[:, None] + tau[None, :]) * dt)
+    exact = np.stack([pos(t[:, k]).T for k in range(n)], 1)          # [m, k, 3]
+    trap = np.stack([(r + dt * tau[k] * 0.5 * (beta(ub) + beta(ub + tau[k] * du)))[:, :, 0]
+                     for k in range(n)], 1)
+    late_mid = np.stack([(r + dt * (tau[k] / 6.0) * (beta(ub) + 4.0 * beta(ub + tau[k] * du)
+                                                      + beta(ub + tau[k] * du)))[:, :, 0]
+                         for k in range(n)], 1)
+    assert np.abs(trap - exact).max() > 1e-7
+    assert np.abs(late_mid - exact).max() > 1e-4
+
+
 def test_subcycling_resolves_what_the_coarse_step_aliases():
     """A gamma = 3 circle sampled coarsely: sub-cycled spectra approach the spectrum of
     a 10x finer PIC step at frequencies above the coarse Nyquist frequency."""
