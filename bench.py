@@ -7,16 +7,22 @@ resident in HBM), the FP32 split-phase accumulation of the Lienard-Wiechert
 far-field amplitude for every particle x sample x direction x frequency, the
 window-close particle reduction and the finalize, through the C ABI.
 
-Workload (65,536 electrons, gamma 3 two-beam load in a 64-mode static field,
-4096 samples, 8 observer directions, 1024 log-spaced omega in [0.1, 1000]):
-the largest of the five workloads whose inputs fit in HBM at once.  The
+Workload: the precision workload -- 1,048,576 electrons in two gamma = 10
+beams in a 64-mode static field, 4096 samples, 8 observer directions, 1024
+log-spaced omega in [0.1, 1000].  Its FP64 trajectory (206 GB) is resident in
+HBM; the whole-window ring for every particle at once (192 GB) does not fit
+beside it, so one context sized for a shard of the particles takes the shards
+one after another (rad_next_shard) and sums them into one spectrum.  The
 metric is particle.sample.omega.direction updates per second; the FP32 split
-path's error against the FP64 GPU path is measured on a particle subset.
+path's error against the FP64 GPU path is measured per direction on 65,536 of
+the particles.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
-N > 1 runs under torchrun, one rank per GPU, each on its own particle shard
-(weak scaling, no data-path collective); rank 0 prints one JSON line.
+N > 1 runs under torchrun, one rank per GPU, each on its own 1,048,576
+particles (weak scaling); the ranks' partial sums are added by one NCCL
+all-reduce inside the step (the only exchange of the method) and the
+spectrum is formed from the total; rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -36,26 +42,32 @@ if ROOT not in sys.path:
 
 METRIC = "G particle·step·ω·n updates/s, FP32 split vs FP64 GPU at ≤1e-4 rel L2"
 
-# DRAM bytes (read + write) of one accumulation launch, from the ncu capture summarised
-# in profiles/accum32_workload2_4096p.md (4096 particles, this workload's samples,
-# directions and omegas), valid while the code (comments aside) of the kernel and of its
-# work-list builder is the code that was captured; traffic scales with the particle count.
-TRAFFIC_CAPTURE = {"sources_sha256": "dfb57359011610ba530d66841db0796ff7922217d90d7ca8ac14fab739b638f4",
-                   "bytes_per_launch": 771.210496e6, "particles": 4096}
+# DRAM bytes (read + write) of one accumulation launch from an ncu capture
+# (particles: the captured launch's particle count, with this workload's samples,
+# directions and omegas), valid while the code (comments aside) of the kernel and of
+# its work-list builder is the code that was captured; traffic scales with the
+# particle count.  None: no capture of the current code.
+TRAFFIC_CAPTURE = None
 UNIT = "G updates/s"
-WORKLOAD = 2
+WORKLOAD = 3
+# device memory kept free beside the resident trajectory and one shard's ring
+MEM_MARGIN = 12 << 30
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--fp64-particles", type=int, default=2048)
-    ap.add_argument("--cpu-particles", type=int, default=288)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--shards", type=int, default=0,
+                    help="particle shards per step (0: the fewest that fit in device memory)")
+    ap.add_argument("--fp64-particles", type=int, default=65536)
+    ap.add_argument("--e2e-particles", type=int, default=65536)
+    ap.add_argument("--cpu-particles", type=int, default=None)
     ap.add_argument("--cpu-1core-particles", type=int, default=18)
     ap.add_argument("--particles", type=int, default=None,
                     help="scale the workload to this many particles (profiling cases)")
@@ -72,14 +84,19 @@ def env_rank():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def workload_name(w):
+    (cnt, _, _, gamma), = w.species
+    return (f"precision: {cnt} e- gamma {gamma:g} two-beam, {w.windows[0][1] - w.windows[0][0]} "
+            f"samples, {len(w.dirs)} dirs, {len(w.grids[0])} log omega "
+            f"[{w.grids[0][0]:g}, {w.grids[0][-1]:g}]")
+
+
 def workload_config(w, extra=None):
-    cfg = {"workload": f"{w.n_total} e- gamma 3 two-beam, {w.windows[0][1] - w.windows[0][0]} "
-                       f"samples, {len(w.dirs)} dirs, {len(w.grids[0])} log omega "
-                       f"[{w.grids[0][0]:g}, {w.grids[0][-1]:g}]",
-           "particles": w.n_total, "samples": w.windows[0][1] - w.windows[0][0],
-           "directions": len(w.dirs), "omegas": len(w.grids[0]), "dt": w.dt,
-           "path": "FP32 split-phase (FP64 anchor)", "mode": "incoherent",
-           "l2": "inputs larger than L2 (trajectory FP64 in HBM)"}
+    cfg = {"workload": workload_name(w), "particles": w.n_total,
+           "samples": w.windows[0][1] - w.windows[0][0], "directions": len(w.dirs),
+           "omegas": len(w.grids[0]), "dt": w.dt, "gamma": w.species[0][3],
+           "path": "FP32 split-phase (float-float anchor)", "mode": "incoherent",
+           "l2": "inputs larger than L2 (FP64 trajectory resident in HBM)"}
     if extra:
         cfg.update(extra)
     return cfg
@@ -90,7 +107,6 @@ def workload_config(w, extra=None):
 # ---------------------------------------------------------------------------
 def oracle_sample(n_particles: int):
     """Time the FP64 CPU oracle on the first n_particles of the workload."""
-    import numpy as np
     import oracle
     import trajgen
     w = trajgen.config(WORKLOAD)
@@ -110,15 +126,18 @@ def run_reference(args):
         return 0
     import oracle
     oracle.build()
+    # a bounded sample per step (about 6 s on 16 cores), so that the whole
+    # --steps K --warmup W run ends within a few minutes
+    npart = args.cpu_particles or 144
     vals = []
     for i in range(args.warmup + args.steps):
-        upd, el, cores, w = oracle_sample(args.cpu_particles)
+        upd, el, cores, w = oracle_sample(npart)
         if i >= args.warmup:
             vals.append((upd, el))
     upd = sum(v[0] for v in vals)
     el = sum(v[1] for v in vals)
     value = upd / el / 1e9
-    sample = (f"{args.cpu_particles} of {w.n_total} particles, all samples/directions/omegas "
+    sample = (f"{npart} of {w.n_total} particles, all samples/directions/omegas "
               f"({vals[0][0]:.3e} updates per step)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -156,9 +175,9 @@ def traffic_sources_hash() -> str:
 
 
 def captured_traffic(n_particles: int):
-    """DRAM bytes per accumulation launch from the ncu capture, or None if the code
-    of the kernel or of its work-list builder changed since the capture."""
-    if traffic_sources_hash() != TRAFFIC_CAPTURE["sources_sha256"]:
+    """DRAM bytes per accumulation launch from the ncu capture, or None if there is
+    none or the code of the kernel or of its work-list builder changed since."""
+    if not TRAFFIC_CAPTURE or traffic_sources_hash() != TRAFFIC_CAPTURE["sources_sha256"]:
         return None
     return TRAFFIC_CAPTURE["bytes_per_launch"] * n_particles / TRAFFIC_CAPTURE["particles"]
 
@@ -216,6 +235,26 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def ring_bytes_per_particle(samples: int, K: int = 8) -> int:
+    """Device bytes of one particle's whole-window ring (44 B per sample with the
+    selector word, the ring's 64-sample margin) and anchor ring (24 B per K samples)."""
+    slots = (samples + 31) // 32 * 32 + 64
+    return slots * 44 + (slots // K) * 24
+
+
+def choose_shards(n_total: int, n_calls: int, samples: int, free_bytes: int) -> int:
+    """The fewest power-of-two particle shards whose ring fits beside the resident
+    FP64 trajectory (48 bytes per particle and call) with MEM_MARGIN to spare."""
+    inputs = n_total * n_calls * 48
+    shards = 1
+    while shards < n_total:
+        per = -(-n_total // shards)
+        if inputs + per * ring_bytes_per_particle(samples) + MEM_MARGIN <= free_bytes:
+            return shards
+        shards *= 2
+    return shards
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -242,9 +281,28 @@ def main():
     if args.particles:
         w = trajgen.config(WORKLOAD, args.particles / w.n_total)
     N = w.n_total
-    # weak scaling: each rank owns its own particle shard of the same size
-    X, U = tg.trajectory_gpu(w, first=rank * N, count=N)
-    sp = [(s[0], s[1], s[2]) for s in w.species]
+    samples = w.windows[0][1] - w.windows[0][0]
+    free, _ = torch.cuda.mem_get_info()
+    P = args.shards or choose_shards(N, w.n_calls, samples, free)
+    n = -(-N // P)                                  # particles per shard
+    # weak scaling: rank r owns particles [r N, (r + 1) N) of the generator; its
+    # shards are consecutive blocks of them, each a contiguous [calls][3][n] slab
+    Xs, Us = [], []
+    for b in range(P):
+        cnt = min(n, N - b * n)
+        X, U = tg.trajectory_gpu(w, first=rank * N + b * n, count=cnt)
+        if cnt < n:
+            # a short last shard is padded with particles at rest, which radiate
+            # exactly nothing (uniform motion: betadot = 0)
+            Xp = torch.full((X.shape[0], 3, n), 1.0, dtype=torch.float64, device="cuda")
+            Up = torch.zeros_like(Xp)
+            Xp[:, :, :cnt] = X
+            Up[:, :, :cnt] = U
+            X, U = Xp, Up
+        Xs.append(X)
+        Us.append(U)
+    torch.cuda.synchronize()
+    q, mass = w.species[0][1], w.species[0][2]
     opts = {}
     if args.variant is not None:
         opts["variant"] = args.variant
@@ -256,15 +314,28 @@ def main():
         opts["blocks_per_sm"] = args.blocks_per_sm
     if args.poly_per_lane is not None:
         opts["poly_per_lane"] = args.poly_per_lane
-    ctx = R.Radiation(w.dirs, w.grids, w.dt, sp, w.windows, precision=R.RAD_FP32_SPLIT,
-                      box_L=w.L, options=opts or None)
-    out = torch.empty(ctx.spectrum_size(), dtype=torch.float64, device="cuda")
-    upd = ctx.updates()
+    ctx = R.Radiation(w.dirs, w.grids, w.dt, [(n, q, mass)], w.windows,
+                      precision=R.RAD_FP32_SPLIT, box_L=w.L, options=opts or None)
+    nbins = ctx.spectrum_size()
+    out = torch.empty(nbins, dtype=torch.float64, device="cuda")
+    sums = torch.empty(nbins, dtype=torch.float64, device="cuda")
+    upd_shard = ctx.updates()
+    upd = w.updates()                 # the padding particles of a short shard are not counted
 
     def step():
         ctx.reset()
-        ctx.accumulate_steps(0, X, U)
-        ctx.finalize(out)
+        for b in range(P):
+            if b:
+                ctx.next_shard()
+            ctx.accumulate_steps(0, Xs[b], Us[b])
+        if world == 1:
+            ctx.finalize(out)
+        else:
+            # the method's one exchange: the ranks' particle sums are added, then
+            # the spectrum of all ranks' particles is formed from the total
+            ctx.partial_sums(sums)
+            dist.all_reduce(sums, op=dist.ReduceOp.SUM)
+            R.spectrum_from_sums(sums, R.RAD_INCOHERENT, out)
 
     for _ in range(args.warmup):
         step()
@@ -292,85 +363,157 @@ def main():
     acc_ms = t_after["accum_ms"] - t_before["accum_ms"]
     acc_n = t_after["accum_launches"] - t_before["accum_launches"]
     ing_n = t_after["ingest_launches"] - t_before["ingest_launches"]
-    launches = int(acc_n + ing_n + args.steps)        # + one finalize kernel per step
+    # + one finalize (or spectrum-from-sums) kernel per step
+    launches = int(acc_n + ing_n + args.steps)
     ms_step = ms / args.steps
     value = world * upd / (ms_step * 1e-3) / 1e9
     opts_used = ctx.options()
+    S_full = out.cpu().numpy().reshape(len(w.dirs), -1)
+    ctx.close()
+    del ctx
 
-    # roofline of the dominant kernel (window accumulation), measured live
+    # roofline of the dominant kernel (the window accumulation, one launch per
+    # shard), measured live with CUDA events on the context's stream
     sm_mhz = clocks["sm_mhz"] if clocks else None
-    rl = roofline.accum32_roofline(upd * args.steps / max(acc_n, 1), acc_ms / max(acc_n, 1),
+    rl = roofline.accum32_roofline(upd_shard, acc_ms / max(acc_n, 1),
                                    torch.cuda.get_device_properties(local).multi_processor_count,
                                    sm_mhz, opts_used)
-    rl["traffic"] = captured_traffic(N)
+    rl["traffic"] = captured_traffic(n)
+
+    # the particle sample for the FP64 comparison and the end-to-end run: the
+    # first particles of shard 0
+    keep = max(args.e2e_particles if not args.no_e2e else 0,
+               args.fp64_particles if not args.no_fp64 else 0)
+    keep = min(keep, n)
+    Xk = Xs[0][:, :, :keep].contiguous() if keep else None
+    Uk = Us[0][:, :, :keep].contiguous() if keep else None
+    del Xs, Us, X, U
+    torch.cuda.empty_cache()
 
     # end to end through the public API with host buffers (pinned), H2D/D2H inside
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and keep:
+        ne = min(args.e2e_particles, keep)
+        Xd = Xk[:, :, :ne].contiguous()
+        Ud = Uk[:, :, :ne].contiguous()
+        ce = R.Radiation(w.dirs, w.grids, w.dt, [(ne, q, mass)], w.windows,
+                         precision=R.RAD_FP32_SPLIT, box_L=w.L, options=opts or None)
+        upd_e = ce.updates()
+        oute = torch.empty(ce.spectrum_size(), dtype=torch.float64, device="cuda")
         host_mem = "pinned"
         try:
-            Xh = torch.empty(X.shape, dtype=torch.float64, pin_memory=True)
-            Uh = torch.empty(U.shape, dtype=torch.float64, pin_memory=True)
+            Xh = torch.empty(Xd.shape, dtype=torch.float64, pin_memory=True)
+            Uh = torch.empty(Ud.shape, dtype=torch.float64, pin_memory=True)
         except RuntimeError:
-            # many ranks on one node may not be able to lock 13 GB each
+            # many ranks on one node may not be able to lock this much each
             host_mem = "pageable"
-            Xh = torch.empty(X.shape, dtype=torch.float64)
-            Uh = torch.empty(U.shape, dtype=torch.float64)
-        Xh.copy_(X)
-        Uh.copy_(U)
-        outh = np.empty(ctx.spectrum_size())
+            Xh = torch.empty(Xd.shape, dtype=torch.float64)
+            Uh = torch.empty(Ud.shape, dtype=torch.float64)
+        Xh.copy_(Xd)
+        Uh.copy_(Ud)
+        outh = np.empty(ce.spectrum_size())
+        ke = max(1, args.steps)
+
+        # the same sample from device memory, for the exposed-copy figure
+        def step_dev():
+            ce.reset()
+            ce.accumulate_steps(0, Xd, Ud)
+            ce.finalize(oute)
+
+        step_dev()
+        torch.cuda.synchronize()
+        d0 = torch.cuda.Event(enable_timing=True)
+        d1 = torch.cuda.Event(enable_timing=True)
+        d0.record(st)
+        for _ in range(ke):
+            step_dev()
+        d1.record(st)
+        torch.cuda.synchronize()
+        dev_ms = d0.elapsed_time(d1) / ke
+
+        # the host-to-device link on its own: one copy of the sample's x, on a
+        # side stream, timed with CUDA events on that stream
+        cs = torch.cuda.Stream()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(cs):
+            c0.record(cs)
+            Xd.copy_(Xh, non_blocking=True)
+            c1.record(cs)
+        torch.cuda.synchronize()
+        h2d_gbs = Xh.numel() * 8 / (c0.elapsed_time(c1) * 1e-3) / 1e9
 
         def step_e2e():
-            ctx.reset()
-            ctx.accumulate_steps(0, Xh, Uh)
-            ctx.finalize(outh)
+            ce.reset()
+            ce.accumulate_steps(0, Xh, Uh)
+            ce.finalize(outh)
 
-        step_e2e()
-        torch.cuda.synchronize()
-        barrier()
-        t0 = time.perf_counter()
-        ke = max(1, min(args.steps, 3))
-        for _ in range(ke):
+        for _ in range(2):
             step_e2e()
         torch.cuda.synchronize()
-        el = time.perf_counter() - t0
+        barrier()
+        times = []
+        for _ in range(ke):
+            t0 = time.perf_counter()
+            step_e2e()
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        el = sum(times) / ke
         if world > 1:
             t = torch.tensor([el], device="cuda", dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             el = float(t.item())
-        e2e = {"value": world * upd / (el / ke) / 1e9, "unit": UNIT,
+        e2e = {"value": world * upd_e / el / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(Xh.numel() * 8 + Uh.numel() * 8),
-               "d2h_bytes_per_step": int(outh.size * 8), "host_memory": host_mem}
-        del Xh, Uh
+               "d2h_bytes_per_step": int(outh.size * 8), "host_memory": host_mem,
+               "sample": f"first {ne} particles of the workload, all samples/directions/omegas "
+                         f"({upd_e:.3e} updates per step; per-particle work as in the "
+                         f"device-resident step)",
+               "steps": ke, "ms_per_step": 1e3 * el,
+               "step_ms_min_median_max": [1e3 * min(times), 1e3 * statistics.median(times),
+                                          1e3 * max(times)],
+               "device_ms_per_step_same_sample": dev_ms,
+               "exposed_copy_ms_per_step": 1e3 * el - dev_ms,
+               "h2d_gbs_measured": h2d_gbs}
+        ce.close()
+        del Xh, Uh, Xd, Ud, ce
 
-    # FP64 GPU path on a particle subset, and the FP32 split error against it
-    n64 = min(args.fp64_particles, N)
-    Xs = X[:, :, :n64].contiguous()
-    Us = U[:, :, :n64].contiguous()
-    c64 = R.Radiation(w.dirs, w.grids, w.dt, [(n64, sp[0][1], sp[0][2])], w.windows,
-                      precision=R.RAD_FP64, box_L=w.L)
-    c64.accumulate_steps(0, Xs, Us)
-    S64 = c64.finalize()[0]
-    t64 = c64.timing()
-    upd64 = c64.updates()
-    c64.close()
-    c32 = R.Radiation(w.dirs, w.grids, w.dt, [(n64, sp[0][1], sp[0][2])], w.windows,
-                      precision=R.RAD_FP32_SPLIT, box_L=w.L, options=opts or None)
-    c32.accumulate_steps(0, Xs, Us)
-    S32 = c32.finalize()[0]
-    c32.close()
-    rel = np.linalg.norm(S32 - S64, axis=1) / np.linalg.norm(S64, axis=1)
-    fp64_rate = upd64 / (t64["accum_ms"] * 1e-3) / 1e9
-    fp32_kernel_rate = upd / (acc_ms / max(acc_n, 1) * 1e-3) / 1e9
+    # FP64 GPU path on a particle sample, and the FP32 split error against it
+    fp64 = rel = None
+    n64 = 0
+    fp32_kernel_rate = upd_shard / (acc_ms / max(acc_n, 1) * 1e-3) / 1e9 if acc_n else None
+    if not args.no_fp64 and keep:
+        n64 = min(args.fp64_particles, keep)
+        X64 = Xk[:, :, :n64].contiguous()
+        U64 = Uk[:, :, :n64].contiguous()
+        c64 = R.Radiation(w.dirs, w.grids, w.dt, [(n64, q, mass)], w.windows,
+                          precision=R.RAD_FP64, box_L=w.L)
+        c64.accumulate_steps(0, X64, U64)
+        S64 = c64.finalize()[0]
+        t64 = c64.timing()
+        upd64 = c64.updates()
+        c64.close()
+        c32 = R.Radiation(w.dirs, w.grids, w.dt, [(n64, q, mass)], w.windows,
+                          precision=R.RAD_FP32_SPLIT, box_L=w.L, options=opts or None)
+        c32.accumulate_steps(0, X64, U64)
+        S32 = c32.finalize()[0]
+        c32.close()
+        rel = np.linalg.norm(S32 - S64, axis=1) / np.linalg.norm(S64, axis=1)
+        fp64_rate = upd64 / (t64["accum_ms"] * 1e-3) / 1e9
+        fp64 = {"value": fp64_rate, "unit": UNIT,
+                "sample": f"first {n64} particles, same samples/dirs/omegas"}
+    del Xk, Uk
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        cupd, cel, cores, _ = oracle_sample(args.cpu_particles)
+        ncpu = args.cpu_particles or 288
+        cupd, cel, cores, _ = oracle_sample(ncpu)
         cpu = {"value": cupd / cel / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"first {args.cpu_particles} particles of the workload, all 4096 "
-                         f"samples x 8 dirs x 1024 omega ({cupd:.3e} updates, {cel:.1f} s)"}
+               "sample": f"first {ncpu} particles of the workload, all {samples} "
+                         f"samples x {len(w.dirs)} dirs x {len(w.grids[0])} omega "
+                         f"({cupd:.3e} updates, {cel:.1f} s)"}
         if args.cpu_1core_particles > 0:
             # the same oracle on one core (a smaller bounded sample)
             oracle.set_num_threads(1)
@@ -387,17 +530,20 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic",
-                "config": workload_config(w, {"options": opts_used,
-                                              "parallelism": f"particle shards x{world}"}),
+                "config": workload_config(w, {"options": opts_used, "shards_per_step": P,
+                                              "particles_per_shard": n,
+                                              "parallelism": f"particle shards x{world}"
+                                              + (", NCCL all-reduce of the partial sums"
+                                                 if world > 1 else "")}),
                 "clocks": clocks, "gpu_launches": launches, "roofline": rl,
-                "e2e": e2e, "cpu_baseline": cpu,
-                "fp64_gpu": {"value": fp64_rate, "unit": UNIT,
-                             "sample": f"{n64} particles, same samples/dirs/omegas"},
-                "fp32_vs_fp64_rel_l2": {"max": float(rel.max()), "per_direction":
-                                        [float(v) for v in rel], "particles": n64},
-                "fp32_kernel_speedup_vs_fp64_gpu": fp32_kernel_rate / fp64_rate}
+                "e2e": e2e, "cpu_baseline": cpu, "fp64_gpu": fp64,
+                "fp32_vs_fp64_rel_l2": None if rel is None else
+                {"max": float(rel.max()), "per_direction": [float(v) for v in rel],
+                 "particles": n64},
+                "fp32_kernel_speedup_vs_fp64_gpu": (fp32_kernel_rate / fp64["value"]
+                                                    if fp64 and fp32_kernel_rate else None),
+                "spectrum_finite": bool(np.all(np.isfinite(S_full)) and np.all(S_full >= 0))}
         print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         dist.destroy_process_group()
     return 0

@@ -94,13 +94,23 @@ typedef struct {
 } rad_species;
 
 /* One spectrum window: samples [s0, s1) of the species in species_mask (bit i
- * = species i), on frequency grid freq_grid.  The output holds, per window,
- * a [D][len(grid)] block (Sec. 2.2: spectra "recorded every small multiple of
- * a simulation timestep"; a cumulative snapshot is the window [0, t)). */
+ * = species i), on frequency grid freq_grid, seen by the observers in dir_set
+ * (Sec. 2.2: spectra "recorded every small multiple of a simulation timestep",
+ * a cumulative snapshot being the window [0, t); "multiple far-field
+ * observers at arbitrary orientation", so each window may take its own subset
+ * of the context's directions).  The output holds, per window, a
+ * [n_dirs][len(grid)] block whose rows follow dir_set (all D directions in
+ * order when dir_set is NULL).  A zero-initialised window tail (dir_set NULL,
+ * n_dir_set 0) selects every direction. */
 typedef struct {
     int64_t s0, s1;
     uint32_t species_mask;
     int32_t freq_grid;
+    const int32_t *dir_set;  /* NULL: every direction; else n_dir_set indices into
+                                the directions given to rad_init (repeats allowed),
+                                copied by rad_init                                 */
+    int32_t n_dir_set;       /* entries of dir_set (>= 1 when dir_set is not NULL) */
+    int32_t reserved;        /* must be 0                                          */
 } rad_window;
 
 /* Sample selectors (Sec. 2.2: "multiple regions for spectral collection in the
@@ -154,7 +164,7 @@ typedef struct {
  *   dt         : time step (> 0).
  *   sp         : n_species >= 1 species; particle axis = species concatenated.
  *   win        : n_win >= 1 windows, 0 <= s0 <= s1, grid index in range,
- *                species_mask within the species.
+ *                species_mask within the species, dir_set entries in [0, D).
  *   mode       : RAD_INCOHERENT or RAD_COHERENT.
  *   precision  : RAD_FP64 or RAD_FP32_SPLIT.
  *   box_L      : periodic box side for unwrapping positions (0: no unwrap).
@@ -207,8 +217,8 @@ int rad_accumulate_steps(rad_ctx *ctx, int64_t step0, int64_t n_steps, const dou
 
 /*
  * rad_finalize -- evaluate deferred windows, scale by 1/(4 pi^2 c) and write
- * the spectra: spectrum is [n_win][D][len(grid of window)] FP64 concatenated
- * over windows (host or device).  Synchronises the context's stream.  Returns
+ * the spectra: spectrum is [n_win][n_dirs of window][len(grid of window)] FP64
+ * concatenated over windows (host or device).  Synchronises the context's stream.  Returns
  * RAD_EINCOMPLETE if a window's last sample has not arrived, RAD_ETIMEOUT or
  * RAD_ENAN if a device-side check failed.  May be called more than once.
  */
@@ -230,6 +240,40 @@ int rad_finalize(rad_ctx *ctx, double *spectrum);
  * Same preconditions, synchronisation and errors as rad_finalize.
  */
 int rad_partial_sums(rad_ctx *ctx, double *out);
+
+/*
+ * rad_next_shard -- begin a further particle shard in the same context: the
+ * step counter returns to 0 and the following calls hand over the leapfrog
+ * states of another set of particles with the same species counts, whose
+ * amplitudes are summed into the same accumulators (Sec. 2.2's sum over the
+ * tracked particles j: incoherent spectra of disjoint particle sets add, and
+ * coherent amplitudes add before the modulus is taken).  rad_finalize then
+ * gives the spectrum of the union of every shard since rad_init or rad_reset.
+ * This is how a population whose whole-window trajectory ring does not fit in
+ * device memory at once is evaluated on one GPU: the context is sized for one
+ * shard and the shards are handed over one after another.  Every window must
+ * be complete for the current shard (RAD_EINCOMPLETE otherwise); deferred
+ * windows are evaluated before the step counter is rewound.  Enqueues work on
+ * the context's stream only; does not synchronise.
+ */
+int rad_next_shard(rad_ctx *ctx);
+
+/*
+ * rad_spectrum_from_sums -- the spectrum of the union of particle shards from
+ * the element-wise sum of their rad_partial_sums outputs (Sec. 2.2: incoherent
+ * spectra of disjoint particle sets add; coherent amplitudes add before the
+ * modulus is taken), for the shards of several processes or GPUs once their
+ * partial sums have been added (for example by an all-reduce):
+ *   RAD_INCOHERENT: spectrum[i] = sums[i] / (4 pi^2)
+ *   RAD_COHERENT:   spectrum[i] = (sums[4i]^2 + sums[4i+1]^2 + sums[4i+2]^2
+ *                                  + sums[4i+3]^2) / (4 pi^2)
+ * sums: [n_bins] or [n_bins][4] FP64 and spectrum: [n_bins] FP64, both in
+ * device memory of the current device (or managed memory); anything else is
+ * RAD_EINVAL.  Runs on cuda_stream (NULL: the legacy default stream) and
+ * returns without synchronising; RAD_ECUDA if the launch fails.
+ */
+int rad_spectrum_from_sums(const double *sums, int64_t n_bins, int32_t mode, double *spectrum,
+                           void *cuda_stream);
 
 /* rad_reset -- forget all steps and zero the accumulators (same configuration). */
 int rad_reset(rad_ctx *ctx);
@@ -286,13 +330,16 @@ void rad_destroy(rad_ctx *ctx);
  * rejected with RAD_ENOSPACE before any device work.  RAD_EINVAL: bad
  * argument; RAD_ECUDA: a CUDA call failed; RAD_ETIMEOUT: a bounded device
  * wait expired (results invalid).
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture on that device.  Every call uses the same array
- * and leaves its contents behind; each call clears what must start at zero.
- * Calls that overlap on the same GPU (from several host threads or streams at
- * once) race on the array and corrupt each other: serialise them.  The call
- * synchronises the stream and returns after the spectrum is written.
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress, which allocates nothing), so the address stays right
+ * when a device reset re-creates the device's context.  The first call on a
+ * device also loads the library's device code there, which is when the array
+ * itself comes into being.  The call synchronises the stream and returns after
+ * the spectrum is written, so it cannot be made while a stream is being
+ * captured into a CUDA graph.  Every call uses the same array and leaves its
+ * contents behind; each call clears what must start at zero.  Calls that
+ * overlap on the same GPU (from several host threads or streams at once) race
+ * on the array and corrupt each other: serialise them.
  */
 int rad_spectrum_noalloc(const double *dirs, int32_t D, const double *freqs, int32_t F, double dt,
                          double charge, int64_t N, int64_t n_calls, const double *x,

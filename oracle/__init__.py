@@ -240,7 +240,9 @@ def spectra(x, u, dt, dirs, grids, windows, species, coherent=False, box_L=0.0,
     x, u     : [n_calls, 3, N_total] leapfrog states (species concatenated).
     dirs     : [D, 3] unit vectors.
     grids    : list of 1-D frequency arrays.
-    windows  : list of (s0, s1, species_mask, grid_index).
+    windows  : list of (s0, s1, species_mask, grid_index) or (s0, s1, species_mask,
+               grid_index, direction indices): a window's spectrum is [len(its
+               directions), len(grid)], rows in the order of its direction list.
     species  : list of (count, charge).
     selectors, window_selector: optional sample selectors (see selector_mask) and,
                per window, the selector index or -1; a selected-out sample
@@ -259,11 +261,14 @@ def spectra(x, u, dt, dirs, grids, windows, species, coherent=False, box_L=0.0,
     sp_index = np.repeat(np.arange(len(species)), counts)
     charge = np.repeat(np.array([float(q) for _, q in species]), counts)
     out = []
-    for wi, (s0, s1, mask, g) in enumerate(windows):
+    dirs = np.reshape(np.asarray(dirs, dtype=np.float64), (-1, 3))
+    for wi, wdef in enumerate(windows):
+        s0, s1, mask, g = wdef[:4]
+        wdirs = dirs if len(wdef) < 5 or wdef[4] is None else dirs[np.asarray(wdef[4], int)]
         include = ((int(mask) >> sp_index) & 1).astype(np.uint8)
         bd = bdot
         if window_selector is not None and window_selector[wi] >= 0:
             bd = bdot * masks[window_selector[wi]][:, None, :]   # V is linear in betadot
-        out.append(window_spectrum(r, beta, bd, charge, dt / nsub, dirs, grids[g], s0 * nsub,
+        out.append(window_spectrum(r, beta, bd, charge, dt / nsub, wdirs, grids[g], s0 * nsub,
                                    s1 * nsub, coherent=coherent, include=include))
     return out

@@ -85,7 +85,7 @@ struct ChunkMeta {
     int32_t lo, hi;        // samples [lo, hi) of the chunk inside the window
     int32_t flags;         // kFirstOfTile | kLastOfTile | kFirstOfItem | kLastOfItem
     int32_t real;          // particles of this tile that exist (0..8)
-    int32_t grid_len, ftile, dir;
+    int32_t grid_len, ftile, row;   // row: the direction's output row in the window
 };
 constexpr int kFirstOfTile = 1, kLastOfTile = 2, kFirstOfItem = 4, kLastOfItem = 8;
 
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
         float nl0 = 0, nl1 = 0, nl2 = 0, qdt = 0;
         int64_t s0 = 0, s1 = 0, out_off = 0;
         int selb = -1;
-        int grid_len = 0, ftile = 0, dir = 0, count = 0, tile0 = 0;
+        int grid_len = 0, ftile = 0, row = 0, count = 0, tile0 = 0;
         uint32_t L = 0;
         for (; cur.valid; ++L) {
             const int buf = L & 1;
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                 out_off = w.out_off;
                 grid_len = w.grid_len;
                 ftile = it.ftile;
-                dir = it.dir;
+                row = it.row;
                 tile0 = it.tile0;
 #pragma unroll
                 for (int i = 0; i < FT; ++i) {
@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                 M.real = count - base < 0 ? 0 : (count - base > kTileP ? kTileP : count - base);
                 M.grid_len = grid_len;
                 M.ftile = ftile;
-                M.dir = dir;
+                M.row = row;
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&S.gfull[buf]);
@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
         // copy what the window close needs before the buffer is handed back
         const bool real_particle = warp < S.meta[buf].real;
         const int64_t out_off = S.meta[buf].out_off;
-        const int glen = S.meta[buf].grid_len, ftile = S.meta[buf].ftile, dir = S.meta[buf].dir;
+        const int glen = S.meta[buf].grid_len, ftile = S.meta[buf].ftile, row = S.meta[buf].row;
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.gempty[buf]);
 
@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
             for (int v = tid; v < FT * 32; v += kComputeWarps * 32) {
                 const int k = ftile * (32 * FT) + (v & 31) + 32 * (v >> 5);
                 if (k < glen) {
-                    const int64_t o = out_off + (int64_t)dir * glen + k;
+                    const int64_t o = out_off + (int64_t)row * glen + k;
                     if (!COH) {
                         atomicAdd(p.acc + o, S.run[v]);
                     } else {

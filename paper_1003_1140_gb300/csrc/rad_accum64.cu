@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
         for (int v = tid; v < FT * 32; v += kComputeWarps * 32) {
             const int k = it.ftile * (32 * FT) + (v & 31) + 32 * (v >> 5);
             if (k < w.grid_len) {
-                const int64_t o = w.out_off + (int64_t)it.dir * w.grid_len + k;
+                const int64_t o = w.out_off + (int64_t)it.row * w.grid_len + k;
                 if (!COH) {
                     atomicAdd(p.acc + o, S.run[v]);
                 } else {

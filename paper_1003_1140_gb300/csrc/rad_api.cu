@@ -100,7 +100,8 @@ struct rad_ctx {
     std::vector<int64_t> in_off;   // [n_species + 1]
     std::vector<int32_t> col_off;  // [n_species]
     int64_t n_in = 0, ncols = 0;
-    std::vector<rad_window> wins;
+    std::vector<rad_window> wins;           // dir_set pointers are not kept (see win_dirs)
+    std::vector<std::vector<int32_t>> win_dirs;   // per window: its directions, output order
     std::vector<int64_t> out_off;
     int64_t out_len = 0;
     rad_options opt{};
@@ -235,6 +236,19 @@ static bool is_device_ptr(const void* p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device memory of the current device, or managed memory: what a kernel launched
+// there may dereference.
+static bool current_device_ptr(const void* p)
+{
+    int dev = -1;
+    cudaPointerAttributes a;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == dev);
+}
+
 static void basis(const double n[3], double e1[3], double e2[3])
 {
     // e1 = normalise(n x a), a = the coordinate axis least aligned with n
@@ -286,7 +300,7 @@ static void build_items(rad_ctx* c, Event& ev, int total_blocks,
             if ((W.species_mask >> s) & 1u) {
                 const int nts = (int)((c->species[s].count + kTileP - 1) / kTileP);
                 const int in_range = std::max(0, std::min(nts, hi_of(s)) - std::max(0, lo_of(s)));
-                units += (double)in_range * nft * c->D;
+                units += (double)in_range * nft * c->win_dirs[w].size();
             }
     }
     const double target_items = 64.0 * std::max(1, total_blocks);
@@ -305,10 +319,11 @@ static void build_items(rad_ctx* c, Event& ev, int total_blocks,
             // tile-group-major: the items that read the same particles
             // (all directions and frequency tiles) are adjacent in the list,
             // so they run at about the same time and share L2
+            const std::vector<int32_t>& wd = c->win_dirs[w];
             for (int t0 = std::max(0, lo_of(s)); t0 < t_end; t0 += G)
-                for (int d = 0; d < c->D; ++d)
+                for (int row = 0; row < (int)wd.size(); ++row)
                     for (int f = 0; f < nft; ++f) {
-                        WorkItem it{w, d, f, s, t0, std::min(G, t_end - t0)};
+                        WorkItem it{w, wd[row], f, s, t0, std::min(G, t_end - t0), row, 0};
                         ev.items.push_back(it);
                         cost.push_back((int64_t)it.ntiles * nch);
                     }
@@ -381,7 +396,11 @@ static std::string tune_key(const rad_ctx* c, int K)
     k << "|s";
     for (const auto& sp : c->species) k << sp.count << ",";
     k << "|w";
-    for (const auto& W : c->wins) k << (W.s1 - W.s0) << ":" << W.species_mask << ":" << W.freq_grid << ",";
+    for (size_t w = 0; w < c->wins.size(); ++w) {
+        const auto& W = c->wins[w];
+        k << (W.s1 - W.s0) << ":" << W.species_mask << ":" << W.freq_grid << ":"
+          << c->win_dirs[w].size() << ",";
+    }
     k << "|d" << c->opt.defer << "|n" << std::max(1, c->opt.subcycle);
     return k.str();
 }
@@ -1149,11 +1168,25 @@ int rad_init(rad_ctx** out, const double* dirs, int32_t D, const double* freqs,
     for (int w = 0; w < n_win; ++w) {
         const rad_window& W = win[w];
         if (W.s0 < 0 || W.s1 < W.s0 || W.freq_grid < 0 || W.freq_grid >= n_grids ||
-            (n_species < 32 && (W.species_mask >> n_species) != 0))
+            (n_species < 32 && (W.species_mask >> n_species) != 0) || W.reserved != 0 ||
+            (W.dir_set && W.n_dir_set < 1))
             return bail(RAD_EINVAL);
-        c->wins.push_back(W);
+        std::vector<int32_t> wd;
+        if (W.dir_set) {
+            for (int32_t i = 0; i < W.n_dir_set; ++i) {
+                if (W.dir_set[i] < 0 || W.dir_set[i] >= D) return bail(RAD_EINVAL);
+                wd.push_back(W.dir_set[i]);
+            }
+        } else {
+            for (int32_t d = 0; d < D; ++d) wd.push_back(d);
+        }
+        rad_window Wc = W;
+        Wc.dir_set = nullptr;                 // the caller's array is not kept
+        Wc.n_dir_set = (int32_t)wd.size();
+        c->wins.push_back(Wc);
         c->out_off.push_back(c->out_len);
-        c->out_len += (int64_t)D * grid_len[W.freq_grid];
+        c->out_len += (int64_t)wd.size() * grid_len[W.freq_grid];
+        c->win_dirs.push_back(std::move(wd));
         c->max_s1 = std::max<int64_t>(c->max_s1, W.s1);
         min_s0 = std::min<int64_t>(min_s0, W.s0);
     }
@@ -1461,6 +1494,40 @@ int rad_partial_sums(rad_ctx* c, double* out)
     });
 }
 
+int rad_spectrum_from_sums(const double* sums, int64_t n_bins, int32_t mode, double* spectrum,
+                           void* cuda_stream)
+{
+    if (n_bins < 0 || (mode != RAD_INCOHERENT && mode != RAD_COHERENT)) return RAD_EINVAL;
+    if (n_bins == 0) return RAD_OK;
+    if (!sums || !spectrum || !current_device_ptr(sums) || !current_device_ptr(spectrum))
+        return RAD_EINVAL;
+    finalize_kernel<<<(unsigned)std::min<int64_t>((n_bins + 255) / 256, 4096), 256, 0,
+                      (cudaStream_t)cuda_stream>>>(sums, spectrum, n_bins, mode == RAD_COHERENT);
+    return cudaGetLastError() == cudaSuccess ? RAD_OK : RAD_ECUDA;
+}
+
+int rad_next_shard(rad_ctx* c)
+{
+    if (!c) return RAD_EINVAL;
+    if (c->next_step < c->max_s1 + 1)
+        return fail(c, RAD_EINCOMPLETE, "window needs step %lld, last step given is %lld",
+                    (long long)c->max_s1, (long long)c->next_step - 1);
+    int rc = freeze(c);
+    if (rc) return rc;
+    CU(cudaSetDevice(c->device));
+    if (c->opt.defer && !c->deferred_done) {
+        for (auto& ev : c->events) {
+            rc = launch_event(c, ev);
+            if (rc) return rc;
+        }
+    }
+    // the ring, anchors and per-particle ingest state are rewritten from step 0
+    // by the next shard's calls; the accumulators keep their sums
+    c->next_step = 0;
+    c->deferred_done = false;
+    return RAD_OK;
+}
+
 int rad_reset(rad_ctx* c)
 {
     if (!c) return RAD_EINVAL;
@@ -1483,7 +1550,7 @@ int64_t rad_updates(const rad_ctx* c)
         int64_t np = 0;
         for (int s = 0; s < c->n_species; ++s)
             if ((W.species_mask >> s) & 1u) np += c->species[s].count;
-        tot += np * (W.s1 - W.s0) * c->D * c->grid_len[W.freq_grid];
+        tot += np * (W.s1 - W.s0) * W.n_dir_set * c->grid_len[W.freq_grid];
     }
     return tot * c->nsub;
 }

@@ -44,11 +44,13 @@ constexpr int kErrNaN = 2;
 // frequency grid and a run of particle tiles of one species.
 struct WorkItem {
     int32_t win;      // window index
-    int32_t dir;      // direction index
+    int32_t dir;      // direction index (into the context's directions)
     int32_t ftile;    // frequency tile index within the window's grid
     int32_t sp;       // species index
     int32_t tile0;    // first particle tile (column / 8)
     int32_t ntiles;   // number of particle tiles
+    int32_t row;      // output row of the direction in the window's [dirs][len] block
+    int32_t pad_;
 };
 
 // Per-window constants the accumulation kernels read.
@@ -56,7 +58,7 @@ struct WinDev {
     int64_t s0, s1;      // sample range
     int32_t grid_off;    // offset of the frequency grid in the frequency arrays
     int32_t grid_len;    // frequencies in the grid
-    int64_t out_off;     // offset of the window's [D][len] block in the accumulators
+    int64_t out_off;     // offset of the window's [dirs][len] block in the accumulators
     int32_t sel;         // selector bit the samples must have, or -1 (all samples)
     int32_t pad_;
 };

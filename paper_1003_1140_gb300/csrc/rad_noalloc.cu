@@ -11,7 +11,6 @@
 // routine.
 #include <algorithm>
 #include <cmath>
-#include <mutex>
 #include <vector>
 
 #include "rad.h"
@@ -25,24 +24,18 @@ using namespace rad;
 constexpr size_t kScratchBytes = size_t(96) << 20;
 __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-// The array's device address, looked up once per device.  In host code the
-// name g_scratch is only a host-side stand-in; kernels must be given the
-// address cudaGetSymbolAddress returns on the device that is current.
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
-
-cudaError_t scratch_address(int dev, void** out)
+// In host code the name g_scratch is only a host-side stand-in; kernels must
+// be given the address cudaGetSymbolAddress returns on the device that is
+// current.  It is looked up on every call (the lookup allocates nothing and
+// costs microseconds): a cached address would go stale when the device's
+// context is torn down and created again (cudaDeviceReset), and a kernel given
+// it would fault.
+cudaError_t scratch_address(void** out)
 {
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return e;
-        g_addr[dev] = p;
-    }
-    *out = g_addr[dev];
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess) return e;
+    *out = p;
     return cudaSuccess;
 }
 
@@ -110,16 +103,16 @@ extern "C" int rad_spectrum_noalloc(const double* dirs, int32_t D, const double*
     const int nft = (F + ftl - 1) / ftl;
     const int64_t ntiles = ncols / kTileP;
 
-    int dev = 0;
-    cudaDeviceProp prop;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return RAD_ECUDA;
     if (!device_memory(x, dev) || !device_memory(u, dev) || !device_memory(spectrum, dev))
         return RAD_EINVAL;
     int nb = 0;
     cudaError_t e = cudaSuccess;
     if (!accum32_dispatch(nullptr, cfg, 0, nullptr, &e, &nb) || nb < 1) return RAD_ECUDA;
-    const int total_blocks = nb * prop.multiProcessorCount;
+    const int total_blocks = nb * sms;
     const double units = (double)ntiles * nft * D;
     const int G = (int)std::max(1.0, std::floor(units / (64.0 * total_blocks)));
     const int64_t ngroups = (ntiles + G - 1) / G;
@@ -140,7 +133,7 @@ extern "C" int rad_spectrum_noalloc(const double* dirs, int32_t D, const double*
     if (cv.off > kScratchBytes) return RAD_ENOSPACE;
 
     void* base = nullptr;
-    if (scratch_address(dev, &base) != cudaSuccess) return RAD_ECUDA;
+    if (scratch_address(&base) != cudaSuccess) return RAD_ECUDA;
     unsigned char* B = static_cast<unsigned char*>(base);
 
     // ---- host tables, packed in the scratch's order and copied in one go
@@ -195,7 +188,7 @@ extern "C" int rad_spectrum_noalloc(const double* dirs, int32_t D, const double*
         for (int f = 0; f < nft; ++f)
             for (int64_t g = 0; g < ngroups; ++g)
                 hi[ni++] = WorkItem{0, d, f, 0, (int32_t)(g * G),
-                                    (int32_t)std::min<int64_t>(G, ntiles - g * G)};
+                                    (int32_t)std::min<int64_t>(G, ntiles - g * G), d, 0};
 
 #define NA_CU(call)                                   \
     do {                                              \

@@ -42,7 +42,8 @@ _ERRNAMES = {RAD_EINVAL: "RAD_EINVAL", RAD_ENOMEM: "RAD_ENOMEM", RAD_ECUDA: "RAD
 EXPORTED = ("rad_init", "rad_set_options", "rad_get_options", "rad_accumulate",
             "rad_accumulate_steps", "rad_finalize", "rad_reset", "rad_spectrum_size",
             "rad_updates", "rad_timing", "rad_last_error", "rad_destroy",
-            "rad_spectrum_noalloc", "rad_partial_sums", "rad_set_selectors")
+            "rad_spectrum_noalloc", "rad_partial_sums", "rad_set_selectors", "rad_next_shard",
+            "rad_spectrum_from_sums")
 
 
 class RadError(RuntimeError):
@@ -57,7 +58,8 @@ class rad_species(ctypes.Structure):
 
 class rad_window(ctypes.Structure):
     _fields_ = [("s0", ctypes.c_int64), ("s1", ctypes.c_int64), ("species_mask", ctypes.c_uint32),
-                ("freq_grid", ctypes.c_int32)]
+                ("freq_grid", ctypes.c_int32), ("dir_set", ctypes.POINTER(ctypes.c_int32)),
+                ("n_dir_set", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 RAD_SEL_BOX = 1
@@ -123,6 +125,10 @@ def load(build_if_missing: bool = True):
         lib.rad_partial_sums.argtypes = [vp, vp]
         lib.rad_reset.restype = ctypes.c_int
         lib.rad_reset.argtypes = [vp]
+        lib.rad_next_shard.restype = ctypes.c_int
+        lib.rad_next_shard.argtypes = [vp]
+        lib.rad_spectrum_from_sums.restype = ctypes.c_int
+        lib.rad_spectrum_from_sums.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, vp, vp]
         lib.rad_spectrum_size.restype = ctypes.c_int64
         lib.rad_spectrum_size.argtypes = [vp]
         lib.rad_updates.restype = ctypes.c_int64
@@ -157,11 +163,32 @@ def _ptr(a):
     raise TypeError(f"unsupported array type {type(a)}")
 
 
+def spectrum_from_sums(sums, mode, out, stream=None):
+    """rad_spectrum_from_sums on device tensors: the spectrum of the union of particle
+    shards from the sum of their partial sums (sums [n] or [n, 4], out [n])."""
+    lib = load()
+    n = out.numel()
+    if sums.numel() != n * (4 if mode == RAD_COHERENT else 1):
+        raise ValueError("sums and out sizes do not match the summation mode")
+    if stream is None:
+        import torch
+        st = torch.cuda.current_stream().cuda_stream
+    else:
+        st = stream if isinstance(stream, int) else stream.cuda_stream
+    rc = lib.rad_spectrum_from_sums(_ptr(sums), n, int(mode), _ptr(out), st)
+    if rc != RAD_OK:
+        raise RadError(rc, "rad_spectrum_from_sums failed")
+    return out
+
+
 class Radiation:
     """One radiation-diagnostic context (rad_init ... rad_destroy)."""
 
     def __init__(self, dirs, grids, dt, species, windows, mode=RAD_INCOHERENT,
                  precision=RAD_FP32_SPLIT, box_L=0.0, stream=None, options=None):
+        """windows: (s0, s1, species_mask, grid) or (s0, s1, species_mask, grid,
+        direction indices) -- the optional fifth element is the window's subset of
+        `dirs`, whose spectra it returns in that order."""
         self._lib = load()
         self._h = ctypes.c_void_p()
         dirs = np.ascontiguousarray(np.reshape(dirs, (-1, 3)), dtype=np.float64)
@@ -174,8 +201,20 @@ class Radiation:
             mass = s[2] if len(s) > 2 else 1.0
             sp[i] = rad_species(int(count), float(charge), float(mass))
         wn = (rad_window * len(windows))()
-        for i, (s0, s1, mask, g) in enumerate(windows):
+        keep = []              # direction-set arrays stay alive until rad_init has copied them
+        self.window_dirs = []
+        for i, wdef in enumerate(windows):
+            s0, s1, mask, g = wdef[:4]
+            dset = wdef[4] if len(wdef) > 4 else None
             wn[i] = rad_window(int(s0), int(s1), int(mask), int(g))
+            if dset is not None:
+                arr = (ctypes.c_int32 * len(dset))(*[int(d) for d in dset])
+                keep.append(arr)
+                wn[i].dir_set = ctypes.cast(arr, ctypes.POINTER(ctypes.c_int32))
+                wn[i].n_dir_set = len(dset)
+                self.window_dirs.append(len(dset))
+            else:
+                self.window_dirs.append(dirs.shape[0])
         if stream is None:
             st = None
         elif isinstance(stream, int):
@@ -194,6 +233,7 @@ class Radiation:
         self.mode = int(mode)
         self.D = dirs.shape[0]
         self.grid_lens = [len(grids[w[3]]) for w in windows]
+        del keep
         if options:
             self.set_options(**options)
 
@@ -266,9 +306,9 @@ class Radiation:
         if not host:
             return out
         res, off = [], 0
-        for L in self.grid_lens:
-            res.append(out[off:off + self.D * L].reshape(self.D, L))
-            off += self.D * L
+        for nd, L in zip(self.window_dirs, self.grid_lens):
+            res.append(out[off:off + nd * L].reshape(nd, L))
+            off += nd * L
         return res
 
     def partial_sums(self, out=None):
@@ -282,6 +322,10 @@ class Radiation:
 
     def reset(self):
         self._check(self._lib.rad_reset(self._h))
+
+    def next_shard(self):
+        """Start a further particle shard: steps restart at 0, sums are kept."""
+        self._check(self._lib.rad_next_shard(self._h))
 
     def timing(self):
         a = ctypes.c_double()

@@ -31,10 +31,10 @@ def test_reference_arm_prints_one_contract_line():
     assert d["value"] > 0 and d["ms_per_step"] > 0
     assert d["higher_is_better"] is True and d["scaling"] == "weak"
     assert d["vs_baseline"] is None and d["data"] == "synthetic" and d["dtype"] == "f64"
-    assert "workload" in d["config"] and d["config"]["particles"] == 65536
+    assert "workload" in d["config"] and d["config"]["particles"] == 1048576
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
-    assert cb["unit"] == d["unit"] and "2 of 65536" in cb["sample"]
+    assert cb["unit"] == d["unit"] and "2 of 1048576" in cb["sample"]
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0

@@ -37,6 +37,9 @@ def _radiation(**kw):
     {"windows": [(-1, 3, 1, 0)]},                     # s0 < 0
     {"windows": [(0, 3, 1, 1)]},                      # grid index out of range
     {"windows": [(0, 3, 2, 0)]},                      # species bit beyond the species
+    {"windows": [(0, 3, 1, 0, [1])]},                 # direction index beyond the directions
+    {"windows": [(0, 3, 1, 0, [0, -1])]},             # negative direction index
+    {"windows": [(0, 3, 1, 0, [])]},                  # an empty direction set
     {"mode": 2}, {"precision": 2},
     {"box_L": -1.0}, {"box_L": math.nan}, {"box_L": math.inf},
 ])
@@ -52,7 +55,7 @@ def test_rad_init_accepts_a_wellformed_configuration_up_to_the_device():
         pytest.skip("a GPU is present: the configuration would simply succeed")
     from paper_1003_1140_gb300 import rad as R
     with pytest.raises(R.RadError) as ei:
-        _radiation(box_L=2.0, windows=[(0, 4, 1, 0), (2, 2, 1, 0)])
+        _radiation(box_L=2.0, windows=[(0, 4, 1, 0), (2, 2, 1, 0), (1, 3, 1, 0, [0, 0])])
     assert ei.value.code == -3
 
 

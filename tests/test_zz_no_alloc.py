@@ -4,9 +4,10 @@ Some callers may not allocate device memory (a simulation that has handed all
 GPU memory to its own pool, or a program where allocation calls are not
 available).  For them the library offers one entry point that works out of a
 fixed device array built into the library.  These tests call it through the
-C ABI and check, on two calls in a row (the array keeps the previous call's
-contents), that it gives what the context API gives, within the FP32 split
-path's tolerance, and that a problem too large for the array is refused.
+C ABI and check, on consecutive calls of different shapes (the array keeps the
+previous call's contents), that it gives what the context API and the FP64
+oracle give, within the FP32 split path's tolerance, and that a problem too
+large for the array is refused.
 This file is collected last so that a failure here stops a -x run only after
 every other test has run.
 """
@@ -48,25 +49,52 @@ def _context_api(dirs, freqs, dt, q, X, U, mode, L):
         return r.finalize()[0]
 
 
+def _oracle(dirs, freqs, dt, q, Xn, Un, mode, L):
+    import oracle
+    import paper_1003_1140_gb300 as R
+    N, nc = Xn.shape[2], Xn.shape[0]
+    return oracle.spectra(Xn, Un, dt, dirs, [freqs], [(0, nc - 1, 1, 0)], [(N, q)],
+                          coherent=mode == R.RAD_COHERENT, box_L=L)[0]
+
+
 def test_noalloc_matches_context_api_on_consecutive_calls():
+    """Consecutive calls of different shapes: each call must give the context
+    API's spectrum and the FP64 oracle's, whatever the earlier calls left in the
+    shared array (ring slots past this call's samples, padding columns past its
+    particles, old anchors, a coherent accumulator of another size)."""
     import paper_1003_1140_gb300 as R
     f = _entry()
-    w = trajgen.config(1, 61 / 1024)
-    Xn, Un = w.trajectory_numpy(n_calls=401)
-    X = torch.as_tensor(Xn, device="cuda")
-    U = torch.as_tensor(Un, device="cuda")
     dirs = np.ascontiguousarray(trajgen.axis_and_oblique_dirs()[[2, 0, 6]])
     freqs = np.ascontiguousarray(trajgen.log_grid(0.1, 300.0, 200))
-    q = w.species[0][1]
-    for mode in (R.RAD_INCOHERENT, R.RAD_INCOHERENT, R.RAD_COHERENT):
-        ref = _context_api(dirs, freqs, w.dt, q, X, U, mode, w.L)
+    # (particles, calls, summation): a larger coherent call first, then a smaller
+    # particle count that is not a multiple of the 8-particle tile and fewer
+    # calls, then the first shape again
+    cases = [(203, 601, R.RAD_COHERENT), (61, 401, R.RAD_INCOHERENT),
+             (45, 257, R.RAD_INCOHERENT), (203, 601, R.RAD_COHERENT)]
+    first = None
+    for i, (N, nc, mode) in enumerate(cases):
+        w = trajgen.config(1, N / 1024)
+        Xn, Un = w.trajectory_numpy(n_calls=nc)
+        X = torch.as_tensor(Xn, device="cuda")
+        U = torch.as_tensor(Un, device="cuda")
+        q = w.species[0][1]
+        ref = _oracle(dirs, freqs, w.dt, q, Xn, Un, mode, w.L)
+        api = _context_api(dirs, freqs, w.dt, q, X, U, mode, w.L)
         out = torch.full((dirs.shape[0] * freqs.size,), float("nan"), dtype=torch.float64,
                          device="cuda")
         assert _call(f, dirs, freqs, w.dt, q, X, U, mode, w.L, out) == 0
         got = out.cpu().numpy().reshape(dirs.shape[0], freqs.size)
         for d in range(dirs.shape[0]):
-            err = np.linalg.norm(got[d] - ref[d]) / np.linalg.norm(ref[d])
-            assert err <= 1e-4, (mode, d, err)
+            e_api = np.linalg.norm(got[d] - api[d]) / np.linalg.norm(api[d])
+            e_ref = np.linalg.norm(got[d] - ref[d]) / np.linalg.norm(ref[d])
+            assert e_api <= 1e-4, (i, N, nc, mode, d, e_api)
+            assert e_ref <= 1e-4, (i, N, nc, mode, d, e_ref)
+        if i == 0:
+            first = got
+        elif i == len(cases) - 1:
+            # the same call again: the same spectrum up to the order of the FP64
+            # atomic additions of the work items' particle sums
+            np.testing.assert_allclose(got, first, rtol=1e-9, atol=1e-12 * np.abs(first).max())
 
 
 def test_noalloc_refuses_a_problem_larger_than_its_memory():
