@@ -322,11 +322,10 @@ void rad_destroy(rad_ctx *ctx);
  *   cuda_stream : stream to run on (NULL: the legacy default stream).
  * Limit: the trajectory ring, anchor ring, per-particle state and
  * accumulators must fit in the 96 MiB array -- about
- *   (round_up(n_calls - 1, 32) + 64) * round_up(N, 8) * 44 bytes
+ *   (round_up(n_calls - 1, 32) + 64) * round_up(N, 8) * 40 bytes
  *   + (that many samples / 32) * round_up(N, 8) * 24 bytes + 72 * N bytes
  *   + 8 * D * F bytes (x4 for RAD_COHERENT) + small tables;
- * (44 bytes with the selector flags), 1024 particles x 2000 samples fit,
- * 8192 x 4096 do not.  Larger problems are
+ * 1024 particles x 2000 samples fit, 8192 x 4096 do not.  Larger problems are
  * rejected with RAD_ENOSPACE before any device work.  RAD_EINVAL: bad
  * argument; RAD_ECUDA: a CUDA call failed; RAD_ETIMEOUT: a bounded device
  * wait expired (results invalid).

@@ -16,13 +16,16 @@
 //   when n.beta > 0 (no cancellation at high gamma), else directly.
 //   |A|^2 = |A.e1|^2 + |A.e2|^2: two complex accumulators per (j, n, w).
 // * Phase split: phi_m = phi_ref + dphi_m.  phi_ref is the retarded time at
-//   the block's anchor sample a = K floor(m/K), shifted to the middle of the
-//   block's phase range, carried as a float-float (hi + lo FP32) pair with
-//   FP64-class accuracy; it enters once per K samples through the float-float
-//   product nu_k * phi_ref (nu = w / 2 pi) reduced modulo one turn exactly.
-//   dphi_m = (m - a - (K-1)) dt - n.(r_m - r_a) is formed with compensated
+//   the block's anchor sample a = K floor(m/K) plus the centre h of the
+//   block's offsets (half the offset of its last sample), carried as a
+//   float-float (hi + lo FP32) pair with FP64-class accuracy; it enters once
+//   per K samples through the float-float product nu_k * phi_ref
+//   (nu = w / 2 pi) reduced modulo one turn exactly.
+//   dphi_m = (m - a) dt - h - n.(r_m - r_a) is formed with compensated
 //   (error-free) FP32 arithmetic from the ring's FP32 offsets and rounded
-//   once, so the per-update phase is one FP32 FMA:
+//   once, so |dphi| is at most half the block's phase range (K dt (1 - n.beta)
+//   / 2: tiny towards the head-on directions) and the per-update phase is one
+//   FP32 FMA:
 //   theta = fma(w_k, dphi_m, Theta_k).  GB300's FP64 pipe is 1/64 of FP32
 //   and its latency stalls the warps, so the kernel issues no FP64 at all.
 // * e^{i theta}: by the special-function unit (__sincosf) for the first FT-NP
@@ -91,11 +94,13 @@ constexpr int kFirstOfTile = 1, kLastOfTile = 2, kFirstOfItem = 4, kLastOfItem =
 
 template <int FT, int K, bool COH>
 struct Smem32 {
-    float tbuf[2][kChunk32][kComps][kTileP];          // bulk-copy destinations (producer only)
+    float tbuf[2][kChunk32][kComps][kTileP];          // bulk-copy destinations (producer only;
+                                                      // a chunk fills comps of the kComps rows)
     float tanc[2][kChunk32 / K][6][kTileP];           // the chunk's anchor positions (hi, lo)
     float4 geo[2][kComputeWarps][kChunk32 + 1];       // V1, V2, dphi per particle and sample
     float ths[2][kComputeWarps][kChunk32 / K][FT][32];  // anchor phases per particle, block
     float2 anc[kComputeWarps][kChunk32 / K];          // phi_ref (hi, lo) of the current chunk
+    float csh[kComputeWarps][kChunk32 / K];           // centre of each block's offset range
     float red[kComputeWarps][FT][32];                 // window-close partials
     double run[(COH ? 4 : 1) * FT * 32];              // per-item particle sums (FP64)
     ChunkMeta meta[2];
@@ -162,7 +167,9 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
     extern __shared__ __align__(128) unsigned char smem_raw[];
     auto& S = *reinterpret_cast<Smem32<FT, K, COH>*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    constexpr uint32_t kBytes = sizeof(S.tbuf[0]);
+    // one chunk of the ring: 32 samples x comps components x 8 particles
+    const int cstride = p.comps * kTileP;
+    const uint32_t kBytes = (uint32_t)(kChunk32 * cstride * sizeof(float));
     constexpr int kNRun = (COH ? 4 : 1) * FT * 32;
     constexpr int NS = FT - NP;   // SFU frequencies per thread
 
@@ -214,7 +221,7 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                 const int64_t tile = p.species[it.sp].col0 / kTileP + it.tile0 + q.t;
                 const int64_t slot = (q.c * kChunk32) % p.ring;
                 const int64_t blk = (q.c * NB) % p.nblk;
-                const float* src = p.slab32 + (tile * p.ring + slot) * (kComps * kTileP);
+                const float* src = p.slab32 + (tile * p.ring + slot) * cstride;
                 const float* asrc = p.anc32 + (tile * p.nblk + blk) * (6 * kTileP);
                 fence_proxy_async();
                 mbar_arrive_expect_tx(&S.tfull[buf], kBytes + kAncBytes);
@@ -273,13 +280,28 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
             pending[buf] = false;
             const int64_t c = cur.c;
             // anchor reference phase of (particle pp, block b):
-            //   phi_ref = (a + K - 1) dt - n . r_a,  a = 32 c + K b   (float-float)
+            //   phi_ref = a dt + h - n . r_a,  a = 32 c + K b   (float-float),
+            // h the centre of the block's offsets (a dt - n . r_a + offset = phi_m):
+            // the offsets (m - a) dt - n . (r_m - r_a) rise monotonically from 0
+            // at the anchor (dphi / dt = 1 - n . beta > 0), so h is half the last
+            // sample's offset, and every offset minus h is at most half the
+            // block's phase range -- small where 1 - n . beta is small.  Any h
+            // gives the same phi_m; a stale or non-finite slot (a sample past the
+            // end of the window) falls back to the range's bound.
             if (lane < kTileP * NB) {
                 const int pp = lane & (kTileP - 1), b = lane >> 3;
-                const float ta = (float)(c * kChunk32 + b * K + (K - 1));
+                const float* tl = &S.tbuf[buf][0][0][0] + (b * K + K - 1) * cstride + pp;
+                const float last = (float)(K - 1) * p.dt_hi -
+                                   (n0 * tl[0] + n1 * tl[kTileP] + n2 * tl[2 * kTileP]);
+                float h = 0.5f * last;
+                if (!(fabsf(h) <= (float)K * p.dt_hi)) h = 0.5f * (float)(K - 1) * p.dt_hi;
+                S.csh[pp][b] = h;
+                const float ta = (float)(c * kChunk32 + b * K);
                 ff t = two_prod(ta, p.dt_hi);
                 float e = fmaf(ta, p.dt_lo, t.lo);
-                float sh = t.hi;
+                const ff th = two_sum(t.hi, h);
+                float sh = th.hi;
+                e = e + th.lo;
                 const float nh[3] = {n0, n1, n2}, nlo[3] = {nl0, nl1, nl2};
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
@@ -293,11 +315,12 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                 const float hi = sh + e;
                 S.anc[pp][b] = make_float2(hi, e - (hi - sh));
             }
+            __syncwarp();
             // geometry: round r handles sample 4 r + lane / 8 of particle lane % 8
 #pragma unroll 2
             for (int r = 0; r < kChunk32 / 4; ++r) {
                 const int sm = 4 * r + (lane >> 3), pp = lane & (kTileP - 1);
-                const float* tb = &S.tbuf[buf][sm][0][pp];
+                const float* tb = &S.tbuf[buf][0][0][0] + sm * cstride + pp;
                 const float b0 = tb[3 * kTileP], b1 = tb[4 * kTileP], b2 = tb[5 * kTileP];
                 const float d0 = tb[6 * kTileP], d1 = tb[7 * kTileP], d2 = tb[8 * kTileP];
                 const float g = tb[9 * kTileP];
@@ -312,11 +335,13 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                 float V1 = -(p1 * dn + q1 * kap) * inv;
                 float V2 = -(p2 * dn + q2 * kap) * inv;
                 if (selb >= 0 && !((__float_as_uint(tb[10 * kTileP]) >> selb) & 1u)) V1 = V2 = 0.0f;
-                // dphi = ((sm mod K) - (K - 1)) dt - n . dr, compensated
-                const float ti = (float)((sm & (K - 1)) - (K - 1));
+                // dphi = (sm mod K) dt - h - n . dr, compensated
+                const float ti = (float)(sm & (K - 1));
                 const ff t = two_prod(ti, p.dt_hi);
                 float e = fmaf(ti, p.dt_lo, t.lo);
-                float sh = t.hi;
+                const ff th = two_sum(t.hi, -S.csh[pp][sm / K]);
+                float sh = th.hi;
+                e = e + th.lo;
                 const float dr[3] = {tb[0], tb[kTileP], tb[2 * kTileP]};
                 const float nh[3] = {n0, n1, n2}, nlo[3] = {nl0, nl1, nl2};
 #pragma unroll

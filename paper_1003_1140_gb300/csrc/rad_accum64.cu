@@ -30,7 +30,8 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     auto& S = *reinterpret_cast<Smem64<FT, COH>*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    constexpr uint32_t kBytes = sizeof(S.tbuf[0]);
+    const int cstride = p.comps * kTileP;   // one sample's components x 8 particles
+    const uint32_t kBytes = (uint32_t)(kChunk64 * cstride * sizeof(double));
     constexpr int kNRun = (COH ? 4 : 1) * FT * 32;
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
                     pend_parity[buf] = (L >> 1) & 1;
                     mbar_arrive_expect_tx(&S.full[buf], kBytes);
                     const int64_t slot = (c * kChunk64) % p.ring;
-                    const double* src = p.slab64 + (tile * p.ring + slot) * (kComps * kTileP);
+                    const double* src = p.slab64 + (tile * p.ring + slot) * cstride;
                     bulk_load(&S.tbuf[buf][0][0][0], src, kBytes, &S.full[buf]);
                 }
             }
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
                     const double n0 = __ldg(dv + 0), n1 = __ldg(dv + 1), n2 = __ldg(dv + 2);
                     const double e10 = __ldg(dv + 3), e11 = __ldg(dv + 4), e12 = __ldg(dv + 5);
                     const double e20 = __ldg(dv + 6), e21 = __ldg(dv + 7), e22 = __ldg(dv + 8);
-                    const double* tb = &S.tbuf[buf][lane][0][warp];
+                    const double* tb = &S.tbuf[buf][0][0][0] + lane * cstride + warp;
                     const double r0 = tb[0 * kTileP], r1 = tb[1 * kTileP], r2 = tb[2 * kTileP];
                     const double b0 = tb[3 * kTileP], b1 = tb[4 * kTileP], b2 = tb[5 * kTileP];
                     const double d0 = tb[6 * kTileP], d1 = tb[7 * kTileP], d2 = tb[8 * kTileP];

@@ -118,6 +118,7 @@ struct rad_ctx {
 
     // ring
     int64_t ring = 0, nblk = 0;
+    int comps = kCompsPlain;       // + the selector-flags word once selectors are defined
     float* slab32 = nullptr;
     double* slab64 = nullptr;
     float* anc32 = nullptr;
@@ -492,6 +493,7 @@ static int autotune32(rad_ctx* c, int K)
         p.anc32 = c->anc32;
         p.ring = c->ring;
         p.nblk = c->nblk;
+        p.comps = c->comps;
         p.dt_hi = (float)(c->dt / c->nsub);
         p.dt_lo = (float)(c->dt / c->nsub - (double)p.dt_hi);
         p.acc = c->acc;
@@ -544,8 +546,8 @@ static int freeze(rad_ctx* c)
         CU(cudaFree(slab));
         slab = nullptr;
         c->ring *= c->nsub;
-        CU(cudaMalloc(&slab, (size_t)c->ring * kComps * nc * es));
-        CU(cudaMemset(slab, 0, (size_t)c->ring * kComps * nc * es));
+        CU(cudaMalloc(&slab, (size_t)c->ring * c->comps * nc * es));
+        CU(cudaMemset(slab, 0, (size_t)c->ring * c->comps * nc * es));
         std::vector<WinDev> wd(c->wins.size());
         CU(cudaMemcpy(wd.data(), c->d_wins, wd.size() * sizeof(WinDev), cudaMemcpyDeviceToHost));
         for (size_t w = 0; w < wd.size(); ++w) {
@@ -646,6 +648,7 @@ static int launch_event(rad_ctx* c, Event& ev)
         p.omega = c->d_om64;
         p.slab64 = c->slab64;
         p.ring = c->ring;
+        p.comps = c->comps;
         p.dt = c->dt / c->nsub;
         p.acc = c->acc;
         p.err_word = c->d_err;
@@ -666,6 +669,7 @@ static int launch_event(rad_ctx* c, Event& ev)
         p.anc32 = c->anc32;
         p.ring = c->ring;
         p.nblk = c->nblk;
+        p.comps = c->comps;
         p.dt_hi = (float)(c->dt / c->nsub);
         p.dt_lo = (float)(c->dt / c->nsub - (double)p.dt_hi);
         p.acc = c->acc;
@@ -699,6 +703,7 @@ static IngestParams ingest_params(const rad_ctx* c)
     p.anc32 = c->anc32;
     p.ncols = c->ncols;
     p.ring = c->ring;
+    p.comps = c->comps;
     p.K = c->K;
     p.nblk = c->nblk;
     p.n_species = c->n_species;
@@ -1005,6 +1010,7 @@ static int graph_for(rad_ctx* c, int kind, const IngestParams& ip, StepGraph** o
                 p.anc32 = c->anc32;
                 p.ring = c->ring;
                 p.nblk = c->nblk;
+                p.comps = c->comps;
                 p.dt_hi = (float)(c->dt / c->nsub);
                 p.dt_lo = (float)(c->dt / c->nsub - (double)p.dt_hi);
                 p.acc = c->acc;
@@ -1278,11 +1284,11 @@ int rad_init(rad_ctx** out, const double* dirs, int32_t D, const double* freqs,
     if (c->fault.alloc) return bail(RAD_ENOMEM);
     const int64_t nc = c->ncols;
     if (precision == RAD_FP64) {
-        CUB(cudaMalloc(&c->slab64, (size_t)c->ring * kComps * nc * sizeof(double)));
-        CUB(cudaMemset(c->slab64, 0, (size_t)c->ring * kComps * nc * sizeof(double)));
+        CUB(cudaMalloc(&c->slab64, (size_t)c->ring * c->comps * nc * sizeof(double)));
+        CUB(cudaMemset(c->slab64, 0, (size_t)c->ring * c->comps * nc * sizeof(double)));
     } else {
-        CUB(cudaMalloc(&c->slab32, (size_t)c->ring * kComps * nc * sizeof(float)));
-        CUB(cudaMemset(c->slab32, 0, (size_t)c->ring * kComps * nc * sizeof(float)));
+        CUB(cudaMalloc(&c->slab32, (size_t)c->ring * c->comps * nc * sizeof(float)));
+        CUB(cudaMemset(c->slab32, 0, (size_t)c->ring * c->comps * nc * sizeof(float)));
     }
     CUB(cudaMalloc(&c->x_prev, 3 * nc * sizeof(double)));
     CUB(cudaMalloc(&c->r_prev, 3 * nc * sizeof(double)));
@@ -1361,6 +1367,19 @@ int rad_set_selectors(rad_ctx* c, const rad_selector* sel, int32_t n_sel,
         if (window_selector[w] < -1 || window_selector[w] >= n_sel)
             return fail(c, RAD_EINVAL, "window %zu: selector index out of range", w);
     CU(cudaSetDevice(c->device));
+    if (n_sel > 0 && c->comps == kCompsPlain) {
+        // the samples now carry their selector bits: the ring gains the flags word
+        const size_t es = c->precision == RAD_FP64 ? sizeof(double) : sizeof(float);
+        void*& slab = c->precision == RAD_FP64 ? reinterpret_cast<void*&>(c->slab64)
+                                               : reinterpret_cast<void*&>(c->slab32);
+        CU(cudaStreamSynchronize(c->stream));
+        CU(cudaFree(slab));
+        slab = nullptr;
+        const size_t bytes = (size_t)c->ring * kComps * c->ncols * es;
+        CU(cudaMalloc(&slab, bytes));
+        CU(cudaMemset(slab, 0, bytes));
+        c->comps = kComps;
+    }
     if (n_sel > 0)
         CU(cudaMemcpy(c->d_sel, h.data(), n_sel * sizeof(SelectorDev), cudaMemcpyHostToDevice));
     c->n_sel = n_sel;

@@ -259,23 +259,23 @@ __global__ void __launch_bounds__(64, 8) ingest_kernel(const IngestParams p)
                         }
                         have_anchor = true;
                     }
-                    float* o = p.slab32 + (tile * p.ring + sl) * (kComps * kTileP) + pp;
+                    float* o = p.slab32 + (tile * p.ring + sl) * (p.comps * kTileP) + pp;
                     for (int c = 0; c < 3; ++c) {
                         o[c * kTileP] = (float)(rk[c] - ra[c]);
                         o[(3 + c) * kTileP] = (float)bk[c];
                         o[(6 + c) * kTileP] = (float)bd[c];
                     }
                     o[9 * kTileP] = (float)(1.0 / gk2);
-                    o[10 * kTileP] = __uint_as_float(flags);
+                    if (p.comps > kCompsPlain) o[10 * kTileP] = __uint_as_float(flags);
                 } else {
-                    double* o = p.slab64 + (tile * p.ring + sl) * (kComps * kTileP) + pp;
+                    double* o = p.slab64 + (tile * p.ring + sl) * (p.comps * kTileP) + pp;
                     for (int c = 0; c < 3; ++c) {
                         o[c * kTileP] = rk[c];
                         o[(3 + c) * kTileP] = bk[c];
                         o[(6 + c) * kTileP] = bd[c];
                     }
                     o[9 * kTileP] = 1.0 / gk2;
-                    o[10 * kTileP] = (double)flags;
+                    if (p.comps > kCompsPlain) o[10 * kTileP] = (double)flags;
                 }
             }
         } else if (p.slab32) {
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(64, 8) ingest_kernel(const IngestParams p)
             const float igq = 1.0f / gq;
             const float corr = dus / (gq * gm * (gq + gm));
             const float idt = (float)(1.0 / p.dt);
-            float* o = p.slab32 + (tile * p.ring + slot) * (kComps * kTileP) + pp;
+            float* o = p.slab32 + (tile * p.ring + slot) * (p.comps * kTileP) + pp;
             o[0 * kTileP] = (float)(rp[0] - ra[0]);
             o[1 * kTileP] = (float)(rp[1] - ra[1]);
             o[2 * kTileP] = (float)(rp[2] - ra[2]);
@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(64, 8) ingest_kernel(const IngestParams p)
             o[7 * kTileP] = (du[1] * igq - um[1] * corr) * idt;
             o[8 * kTileP] = (du[2] * igq - um[2] * corr) * idt;
             o[9 * kTileP] = 1.0f / gb2;
-            {
+            if (p.comps > kCompsPlain) {
                 double ubd[3] = {__dmul_rn(0.5, __dadd_rn(up[0], un[0])),
                                  __dmul_rn(0.5, __dadd_rn(up[1], un[1])),
                                  __dmul_rn(0.5, __dadd_rn(up[2], un[2]))};
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(64, 8) ingest_kernel(const IngestParams p)
             const double gp = sqrt(1.0 + (un[0] * un[0] + un[1] * un[1] + un[2] * un[2]));
             const double gb2 = 1.0 + (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
             const double gb = sqrt(gb2);
-            double* o = p.slab64 + (tile * p.ring + slot) * (kComps * kTileP) + pp;
+            double* o = p.slab64 + (tile * p.ring + slot) * (p.comps * kTileP) + pp;
             o[0 * kTileP] = rp[0];
             o[1 * kTileP] = rp[1];
             o[2 * kTileP] = rp[2];
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(64, 8) ingest_kernel(const IngestParams p)
                 o[(6 + c) * kTileP] = (un[c] / gp - up[c] / gm) / p.dt;
             }
             o[9 * kTileP] = 1.0 / gb2;
-            {
+            if (p.comps > kCompsPlain) {
                 double ubd[3] = {__dmul_rn(0.5, __dadd_rn(up[0], un[0])),
                                  __dmul_rn(0.5, __dadd_rn(up[1], un[1])),
                                  __dmul_rn(0.5, __dadd_rn(up[2], un[2]))};

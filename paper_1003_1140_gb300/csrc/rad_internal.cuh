@@ -14,9 +14,10 @@ namespace rad {
 // trajectory ring layout
 // ---------------------------------------------------------------------------
 // Both rings are tile-major: element (tile, slot, c, p) of particle column
-// col = 8 tile + p sits at ((tile * ring + slot) * 10 + c) * 8 + p, so the
+// col = 8 tile + p sits at ((tile * ring + slot) * comps + c) * 8 + p, so the
 // chunk of consecutive slots the kernels stage is one contiguous block.
-// FP32 split path: slab[tile][slot][c][p] float, c = 0..9 =
+// comps is 10, or 11 when sample selectors are defined (the flags word).
+// FP32 split path: slab[tile][slot][c][p] float, c = 0..9 (10) =
 //   dr (3)   : r_m - r_a, the offset from the block's FP64 anchor position
 //   beta (3) : beta_m
 //   bdot (3) : betadot_m (differenced in FP64 before the rounding)
@@ -28,7 +29,8 @@ namespace rad {
 //   samples, so a chunk's anchors are one contiguous block too).
 // FP64 path: slab64[tile][slot][c][p] double with c = r (3, absolute unwrapped),
 // beta (3), bdot (3), g (1), flags (1).
-constexpr int kComps = 11;   // + selector flags (component 10)
+constexpr int kComps = 11;     // components at most (10 + the selector flags)
+constexpr int kCompsPlain = 10;   // without selectors
 constexpr int kTileP = 8;      // particles per tile: one warp each
 constexpr int kChunk32 = 32;   // samples per TMA chunk, FP32 ring
 constexpr int kChunk64 = 16;   // samples per TMA chunk, FP64 ring
@@ -227,6 +229,7 @@ struct IngestParams {
     float* anc32;           // FP32 path: tile-major anchor ring (r_a as hi + lo)
     int64_t ncols;
     int64_t ring;           // samples in the ring
+    int32_t comps;          // ring components per sample (10, or 11 with selector flags)
     int32_t K;              // anchor interval (FP32 path)
     int64_t nblk;           // anchor blocks in the ring
     int32_t n_species;
@@ -271,6 +274,7 @@ struct Accum32Params {
     const float* anc32;       // tile-major anchor ring
     int64_t ring;
     int64_t nblk;
+    int32_t comps;            // ring components per sample (10, or 11 with selector flags)
     float dt_hi, dt_lo;       // dt as a float-float pair
     double* acc;              // incoherent [n_out]; coherent [n_out][4]
     int* err_word;
@@ -288,6 +292,7 @@ struct Accum64Params {
     const double* omega;      // [n_freq]
     const double* slab64;     // tile-major FP64 ring
     int64_t ring;
+    int32_t comps;            // ring components per sample (10, or 11 with selector flags)
     double dt;
     double* acc;
     int* err_word;

@@ -120,7 +120,7 @@ extern "C" int rad_spectrum_noalloc(const double* dirs, int32_t D, const double*
     if (n_items > INT32_MAX) return RAD_ENOSPACE;
 
     Carve cv;
-    const size_t o_slab = cv.take<float>((size_t)ring * kComps * ncols);
+    const size_t o_slab = cv.take<float>((size_t)ring * kCompsPlain * ncols);
     const size_t o_anc = cv.take<float>((size_t)nblk * 6 * ncols);
     const size_t o_state = cv.take<double>((size_t)9 * ncols);
     const size_t o_acc = cv.take<double>((size_t)D * F * (coh ? 4 : 1));
@@ -218,6 +218,7 @@ extern "C" int rad_spectrum_noalloc(const double* dirs, int32_t D, const double*
     ip.anc32 = reinterpret_cast<float*>(B + o_anc);
     ip.ncols = ncols;
     ip.ring = ring;
+    ip.comps = kCompsPlain;
     ip.K = K;
     ip.nblk = nblk;
     ip.n_species = 1;
@@ -242,6 +243,7 @@ extern "C" int rad_spectrum_noalloc(const double* dirs, int32_t D, const double*
     ap.anc32 = ip.anc32;
     ap.ring = ring;
     ap.nblk = nblk;
+    ap.comps = kCompsPlain;
     ap.dt_hi = (float)dt;
     ap.dt_lo = (float)(dt - (double)ap.dt_hi);
     ap.acc = reinterpret_cast<double*>(B + o_acc);

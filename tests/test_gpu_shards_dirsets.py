@@ -92,7 +92,7 @@ def test_next_shard_needs_complete_windows(sharded):
         r.accumulate_steps(0, Xd, Ud)
         with pytest.raises(R.RadError) as ei:
             r.next_shard()
-        assert ei.value.code == R.RAD_EINCOMPLETE
+        assert ei.value.code == R.rad.RAD_EINCOMPLETE
         # a reset context starts a fresh first shard
         r.reset()
         r.accumulate_steps(0, Xd, Ud)
