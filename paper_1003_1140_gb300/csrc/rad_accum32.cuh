@@ -160,10 +160,16 @@ struct ChunkCursor {
     }
 };
 
-template <int FT, int NP, int K, bool COH, int MB>
+// TURNS: the phase is carried in turns (nu = w / 2 pi instead of w) and
+// reduced to [-1/2, 1/2] turn before the special-function unit, whose own
+// reduction of a radian argument loses accuracy in proportion to it (about
+// 1.3e-7 |theta| rad measured on GB300; 3.4e-7 rad flat after the reduction),
+// at the cost of three FP32 adds and a multiply per update.  SFU frequencies only.
+template <int FT, int NP, int K, bool COH, int MB, bool TURNS>
 __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum32Params p)
 {
     static_assert(NP >= 0 && NP < FT, "polynomial frequencies per thread");
+    static_assert(!TURNS || NP == 0, "the turns-reduced phase is an SFU variant");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     auto& S = *reinterpret_cast<Smem32<FT, K, COH>*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -279,22 +285,37 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
             if (!mbar_wait_bounded(&S.tfull[buf], (L >> 1) & 1, abort_flag, p.err_word)) break;
             pending[buf] = false;
             const int64_t c = cur.c;
+            // samples [lo, hi) of this chunk that lie in the window
+            const int64_t cs = c * kChunk32;
+            const int lo = (int)((s0 > cs ? s0 : cs) - cs);
+            const int hi = (int)((s1 < cs + kChunk32 ? s1 : cs + kChunk32) - cs);
             // anchor reference phase of (particle pp, block b):
             //   phi_ref = a dt + h - n . r_a,  a = 32 c + K b   (float-float),
             // h the centre of the block's offsets (a dt - n . r_a + offset = phi_m):
-            // the offsets (m - a) dt - n . (r_m - r_a) rise monotonically from 0
-            // at the anchor (dphi / dt = 1 - n . beta > 0), so h is half the last
-            // sample's offset, and every offset minus h is at most half the
-            // block's phase range -- small where 1 - n . beta is small.  Any h
-            // gives the same phi_m; a stale or non-finite slot (a sample past the
-            // end of the window) falls back to the range's bound.
+            // the offsets (m - a) dt - n . (r_m - r_a) rise monotonically in m
+            // (dphi / dt = 1 - n . beta > 0), so h is the mean of the offsets of
+            // the block's first and last samples inside the window, and every
+            // offset minus h is at most half the block's phase range -- small
+            // where 1 - n . beta is small.  Any h gives the same phi_m; h is taken
+            // from samples of the window only, so that the result does not depend
+            // on what the ring holds outside it (a block outside the window, or a
+            // non-finite offset, takes the range's bound).
             if (lane < kTileP * NB) {
                 const int pp = lane & (kTileP - 1), b = lane >> 3;
-                const float* tl = &S.tbuf[buf][0][0][0] + (b * K + K - 1) * cstride + pp;
-                const float last = (float)(K - 1) * p.dt_hi -
-                                   (n0 * tl[0] + n1 * tl[kTileP] + n2 * tl[2 * kTileP]);
-                float h = 0.5f * last;
-                if (!(fabsf(h) <= (float)K * p.dt_hi)) h = 0.5f * (float)(K - 1) * p.dt_hi;
+                const int bl = b * K;
+                const int mlo = lo > bl ? lo : bl;
+                const int mhi = hi - 1 < bl + K - 1 ? hi - 1 : bl + K - 1;
+                float h = 0.5f * (float)(K - 1) * p.dt_hi;
+                if (mlo <= mhi) {
+                    const float* t0 = &S.tbuf[buf][0][0][0] + mlo * cstride + pp;
+                    const float* t1 = &S.tbuf[buf][0][0][0] + mhi * cstride + pp;
+                    const float o0 = (float)(mlo - bl) * p.dt_hi -
+                                     (n0 * t0[0] + n1 * t0[kTileP] + n2 * t0[2 * kTileP]);
+                    const float o1 = (float)(mhi - bl) * p.dt_hi -
+                                     (n0 * t1[0] + n1 * t1[kTileP] + n2 * t1[2 * kTileP]);
+                    const float hh = 0.5f * (o0 + o1);
+                    if (fabsf(hh) <= (float)K * p.dt_hi) h = hh;
+                }
                 S.csh[pp][b] = h;
                 const float ta = (float)(c * kChunk32 + b * K);
                 ff t = two_prod(ta, p.dt_hi);
@@ -357,9 +378,6 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
             __syncwarp();
             // anchor phases Theta_k = 2 pi frac(nu_k phi_ref) (float-float product,
             // exact reduction to one turn); halved for the polynomial frequencies
-            const int64_t cs = c * kChunk32;
-            const int lo = (int)((s0 > cs ? s0 : cs) - cs);
-            const int hi = (int)((s1 < cs + kChunk32 ? s1 : cs + kChunk32) - cs);
 #pragma unroll 1
             for (int pp = 0; pp < kTileP; ++pp) {
 #pragma unroll 1
@@ -379,7 +397,8 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                         float fr = pr - ((pr + kMagic) - kMagic);
                         fr = fr - ((fr + kMagic) - kMagic);
                         S.ths[buf][pp][b][i][lane] =
-                            (fr + tl) * (i < NS ? 6.28318530717958647f : 3.14159265358979323f);
+                            TURNS ? fr + tl
+                                  : (fr + tl) * (i < NS ? 6.28318530717958647f : 3.14159265358979323f);
                     }
                 }
             }
@@ -438,7 +457,7 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
 #pragma unroll
             for (int i = 0; i < FT; ++i) {
                 const int k = it.ftile * (32 * FT) + lane + 32 * i;
-                const float wk = (k < w.grid_len) ? p.omega[w.grid_off + k] : 0.0f;
+                const float wk = (k < w.grid_len) ? (TURNS ? p.nu_hi : p.omega)[w.grid_off + k] : 0.0f;
                 om[i] = (i < NS) ? wk : 0.5f * wk;
             }
         }
@@ -460,9 +479,15 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                 const float4 gn = S.geo[buf][warp][(l + 1) & (kChunk32 - 1)];
 #pragma unroll
                 for (int i = 0; i < NS; ++i) {
-                    const float tt = fmaf(om[i], gg.z, th[i]);
                     float sn, cs_;
-                    __sincosf(tt, &sn, &cs_);
+                    if (TURNS) {
+                        const float t = fmaf(om[i], gg.z, th[i]);
+                        const float r = t - ((t + kMagic) - kMagic);   // exact, |r| <= 1/2
+                        __sincosf(r * 6.28318530717958647f, &sn, &cs_);
+                    } else {
+                        const float tt = fmaf(om[i], gg.z, th[i]);
+                        __sincosf(tt, &sn, &cs_);
+                    }
                     a1r[i] = fmaf(gg.x, cs_, a1r[i]);
                     a1i[i] = fmaf(gg.x, sn, a1i[i]);
                     a2r[i] = fmaf(gg.y, cs_, a2r[i]);
@@ -554,10 +579,10 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
     }
 }
 
-template <int FT, int NP, int K, bool COH, int MB>
+template <int FT, int NP, int K, bool COH, int MB, bool TURNS = false>
 cudaError_t launch32_one(const Accum32Params& p, int grid, cudaStream_t st)
 {
-    auto kern = accum32_kernel<FT, NP, K, COH, MB>;
+    auto kern = accum32_kernel<FT, NP, K, COH, MB, TURNS>;
     const size_t smem = smem32_bytes<FT, NP, K, COH>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -566,14 +591,14 @@ cudaError_t launch32_one(const Accum32Params& p, int grid, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template <int FT, int NP, int K, bool COH, int MB>
+template <int FT, int NP, int K, bool COH, int MB, bool TURNS = false>
 int blocks32_one()
 {
     int nb = 0;
     const size_t smem = smem32_bytes<FT, NP, K, COH>();
-    if (cudaFuncSetAttribute(accum32_kernel<FT, NP, K, COH, MB>,
+    if (cudaFuncSetAttribute(accum32_kernel<FT, NP, K, COH, MB, TURNS>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, accum32_kernel<FT, NP, K, COH, MB>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, accum32_kernel<FT, NP, K, COH, MB, TURNS>,
                                                       kBlockThreads, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -581,12 +606,19 @@ int blocks32_one()
     return nb;
 }
 
-// One instantiation family: (FT, NP, MB) for every K and both summation modes.
+// One instantiation family: (FT, NP, MB) for every K and both summation modes
+// (radian phase; RAD_ACCUM32_FAMILY_TURNS: the turns-reduced SFU phase).
 #define RAD_ACCUM32_FAMILY(FT, NP, MB)                                                       \
-    if (cfg.ft == FT && cfg.np == NP && cfg.mb == MB) {                                      \
+    if (!cfg.turns && cfg.ft == FT && cfg.np == NP && cfg.mb == MB) {                        \
         if (cfg.K == 8) { if (cfg.coh) FN(FT, NP, 8, true, MB); else FN(FT, NP, 8, false, MB); } \
         if (cfg.K == 16) { if (cfg.coh) FN(FT, NP, 16, true, MB); else FN(FT, NP, 16, false, MB); } \
         if (cfg.K == 32) { if (cfg.coh) FN(FT, NP, 32, true, MB); else FN(FT, NP, 32, false, MB); } \
+    }
+#define RAD_ACCUM32_FAMILY_TURNS(FT, MB)                                                     \
+    if (cfg.turns && cfg.ft == FT && cfg.np == 0 && cfg.mb == MB) {                          \
+        if (cfg.K == 8) { if (cfg.coh) FNT(FT, 8, true, MB); else FNT(FT, 8, false, MB); }     \
+        if (cfg.K == 16) { if (cfg.coh) FNT(FT, 16, true, MB); else FNT(FT, 16, false, MB); }  \
+        if (cfg.K == 32) { if (cfg.coh) FNT(FT, 32, true, MB); else FNT(FT, 32, false, MB); }  \
     }
 
 }  // namespace rad

@@ -271,7 +271,7 @@ bool rad::accum32_dispatch(const Accum32Params* p, const Accum32Config& cfg, int
                            cudaStream_t st, cudaError_t* err, int* nb)
 {
     return accum32_ft8_sfu(p, cfg, grid, st, err, nb) || accum32_ft8_mix(p, cfg, grid, st, err, nb) ||
-           accum32_ft16(p, cfg, grid, st, err, nb);
+           accum32_ft16(p, cfg, grid, st, err, nb) || accum32_ft8_turns(p, cfg, grid, st, err, nb);
 }
 
 static int chunk_len(const rad_ctx* c) { return c->precision == RAD_FP64 ? kChunk64 : kChunk32; }
@@ -304,7 +304,10 @@ static void build_items(rad_ctx* c, Event& ev, int total_blocks,
                 units += (double)in_range * nft * c->win_dirs[w].size();
             }
     }
-    const double target_items = 64.0 * std::max(1, total_blocks);
+    // about 256 items per resident block: the launch ends with every block on its
+    // last item, so an item's length is the tail's scale (1/256 of a block's
+    // work); an item costs one list fetch and one FP64 flush of its sums
+    const double target_items = 256.0 * std::max(1, total_blocks);
     int G = (int)std::max(1.0, std::floor(units / target_items));
     ev.items.clear();
     std::vector<int64_t> cost;
@@ -365,8 +368,11 @@ static cudaEvent_t next_event(std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& 
 // ---------------------------------------------------------------------------
 // autotuner for the FP32 kernel variant (variant = RAD_VARIANT_AUTO)
 // ---------------------------------------------------------------------------
-// Largest anchor interval K whose worst-case phase rounding per update,
-// w_max * |dphi|_max * 2^-24 with |dphi| <= 2 (K - 1) dt, stays within 2e-4 rad.
+// Largest anchor interval K whose worst-case rounding of the offset phase per
+// update, w_max * |dphi|_max * 2^-24, stays within 1e-4 rad; the offsets are
+// centred in their block, so |dphi| <= (K - 1) dt (1 - n.beta) / 2 <= (K - 1) dt.
+// (The radian SFU variants add the unit's own reduction error, about
+// 1.3e-7 |theta| rad; RAD_VARIANT_TURNS removes it.)
 static int budget_K(const rad_ctx* c)
 {
     double wmax = 0.0;
@@ -374,8 +380,8 @@ static int budget_K(const rad_ctx* c)
         for (int k = 0; k < c->grid_len[g]; ++k)
             wmax = std::max(wmax, std::fabs(c->h_freqs[c->grid_off[g] + k]));
     for (int K : {32, 16}) {
-        const double err = wmax * 2.0 * (K - 1) * (c->dt / c->nsub) * std::ldexp(1.0, -24);
-        if (err <= 2e-4) return K;
+        const double err = wmax * (K - 1) * (c->dt / c->nsub) * std::ldexp(1.0, -24);
+        if (err <= 1e-4) return K;
     }
     return 8;
 }
@@ -441,7 +447,42 @@ static void tune_store(const std::string& key, const Accum32Config& cfg)
 
 static int blocks_per_sm(const rad_ctx* c);
 
-// Time the candidate variants on a slice of the real work list (the ring's
+// The autotuner's timing slice: n single-tile items (one particle tile, one
+// direction, one frequency tile, the whole window) of the window with the most
+// samples x frequencies, so that every candidate times the same kind of work
+// and the slice stays a few tens of milliseconds whatever the workload's size.
+static void tune_slice(const rad_ctx* c, Event& ev, size_t n)
+{
+    ev.items.clear();
+    int best = -1;
+    double cost = 0.0;
+    for (size_t w = 0; w < c->wins.size(); ++w) {
+        const rad_window& W = c->wins[w];
+        int64_t np = 0;
+        for (int s = 0; s < c->n_species; ++s)
+            if ((W.species_mask >> s) & 1u) np += c->species[s].count;
+        const double cw = (double)(W.s1 - W.s0) * c->grid_len[W.freq_grid];
+        if (W.s1 > W.s0 && np > 0 && cw > cost) {
+            cost = cw;
+            best = (int)w;
+        }
+    }
+    if (best < 0) return;
+    const rad_window& W = c->wins[best];
+    const int ftl = freq_tile(c);
+    const int nft = (c->grid_len[W.freq_grid] + ftl - 1) / ftl;
+    const std::vector<int32_t>& wd = c->win_dirs[best];
+    for (int s = 0; s < c->n_species && ev.items.size() < n; ++s) {
+        if (!((W.species_mask >> s) & 1u)) continue;
+        const int nt = (int)((c->species[s].count + kTileP - 1) / kTileP);
+        for (int t = 0; t < nt && ev.items.size() < n; ++t)
+            for (int row = 0; row < (int)wd.size() && ev.items.size() < n; ++row)
+                for (int f = 0; f < nft && ev.items.size() < n; ++f)
+                    ev.items.push_back(WorkItem{best, wd[row], f, s, t, 1, row, 0});
+    }
+}
+
+// Time the candidate variants on a slice of single-tile items (the ring's
 // contents do not change the kernel's instruction stream) and keep the fastest.
 static int autotune32(rad_ctx* c, int K)
 {
@@ -471,10 +512,8 @@ static int autotune32(rad_ctx* c, int K)
         if (bps < 1) continue;
         const int total_blocks = bps * c->sms;
         Event ev;
-        for (size_t w = 0; w < c->wins.size(); ++w)
-            if (c->wins[w].s1 > c->wins[w].s0) ev.wins.push_back((int)w);
-        build_items(c, ev, total_blocks);
-        const size_t n = std::min<size_t>(ev.items.size(), (size_t)4 * total_blocks);
+        tune_slice(c, ev, (size_t)16 * total_blocks);
+        const size_t n = ev.items.size();
         if (n == 0) continue;
         WorkItem* d_items = nullptr;
         CU(cudaMalloc(&d_items, n * sizeof(WorkItem)));
@@ -509,8 +548,9 @@ static int autotune32(rad_ctx* c, int K)
             CU(cudaEventSynchronize(e1));
             float ms = 0;
             CU(cudaEventElapsedTime(&ms, e0, e1));
-            // per item, so candidates with different item sizes compare fairly
-            ms_min = std::min(ms_min, ms * (float)ev.items.size() / (float)n);
+            // per item (the items are alike), so candidates with different
+            // numbers of resident blocks compare fairly
+            ms_min = std::min(ms_min, ms / (float)n);
         }
         cudaFree(d_items);
         if (ms_min < best_ms) {
@@ -566,6 +606,7 @@ static int freeze(rad_ctx* c)
         c->cfg.ft = c->opt.freq_per_lane ? c->opt.freq_per_lane : 8;
         c->cfg.np = c->opt.variant == RAD_VARIANT_MIX ? (c->cfg.ft == 8 ? 2 : 4) : 0;
         if (c->opt.variant == RAD_VARIANT_MIX && c->opt.reserved[1] > 0) c->cfg.np = c->opt.reserved[1];
+        c->cfg.turns = c->opt.variant == RAD_VARIANT_TURNS;
         c->cfg.coh = c->mode == RAD_COHERENT;
         c->cfg.mb = c->opt.blocks_per_sm ? c->opt.blocks_per_sm : 2;
         if (c->cfg.ft == 16 && c->cfg.mb != 2)
@@ -1315,7 +1356,10 @@ int rad_set_options(rad_ctx* c, const rad_options* o)
 {
     if (!c || !o) return RAD_EINVAL;
     if (c->frozen) return fail(c, RAD_ESTATE, "options must be set before the first step");
-    if (o->variant < 0 || o->variant > 2) return fail(c, RAD_EINVAL, "variant out of range");
+    if (o->variant < 0 || o->variant > RAD_VARIANT_TURNS)
+        return fail(c, RAD_EINVAL, "variant out of range");
+    if (o->variant == RAD_VARIANT_TURNS && o->freq_per_lane == 16)
+        return fail(c, RAD_EINVAL, "the turns-reduced variant is built for 8 frequencies per thread");
     if (o->anchor_K != 0 && o->anchor_K != 8 && o->anchor_K != 16 && o->anchor_K != 32)
         return fail(c, RAD_EINVAL, "anchor_K must be 0, 8, 16 or 32");
     if (o->freq_per_lane != 0 && o->freq_per_lane != 8 && o->freq_per_lane != 16)
@@ -1400,7 +1444,8 @@ int rad_get_options(const rad_ctx* c, rad_options* o)
         o->anchor_K = c->cfg.K;
         o->freq_per_lane = c->cfg.ft;
         o->blocks_per_sm = c->cfg.mb;
-        o->variant = c->cfg.np > 0 ? RAD_VARIANT_MIX : RAD_VARIANT_SFU;
+        o->variant = c->cfg.turns ? RAD_VARIANT_TURNS
+                     : c->cfg.np > 0 ? RAD_VARIANT_MIX : RAD_VARIANT_SFU;
         o->reserved[1] = c->cfg.np;
     }
     return RAD_OK;

@@ -128,3 +128,34 @@ def test_window_direction_sets(precision, coherent):
     # the repeated direction gives the same row twice (up to the order of the FP64
     # atomic additions of the work items' particle sums)
     np.testing.assert_allclose(got[1][1], got[1][3], rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("coherent", [False, True])
+def test_spectrum_from_summed_partials_on_the_device(sharded, coherent):
+    """The exchange step of the multi-GPU path, on one GPU: two contexts over disjoint
+    particle halves export their partial sums into device buffers, the sums are added
+    (what an all-reduce does across ranks) and rad_spectrum_from_sums forms the
+    spectrum of the union on the device; it equals the oracle's."""
+    R = _rad()
+    w, X, U, dirs, grid, wins, ref = sharded
+    mode = R.RAD_COHERENT if coherent else R.RAD_INCOHERENT
+    halves = [(0, 21), (21, 43)]
+    total = None
+    for a, b in halves:
+        with R.Radiation(dirs, [grid], w.dt, [(b - a, -1.0, 1.0)], wins, mode=mode,
+                         precision=R.RAD_FP64, box_L=w.L) as r:
+            r.accumulate_steps(0, torch.as_tensor(np.ascontiguousarray(X[:, :, a:b]), device="cuda"),
+                               torch.as_tensor(np.ascontiguousarray(U[:, :, a:b]), device="cuda"))
+            part = torch.empty(r.spectrum_size() * (4 if coherent else 1), dtype=torch.float64,
+                               device="cuda")
+            r.partial_sums(part)
+            total = part if total is None else total + part
+    out = torch.empty(total.numel() // (4 if coherent else 1), dtype=torch.float64, device="cuda")
+    R.spectrum_from_sums(total, mode, out)
+    got = out.cpu().numpy()
+    n0 = len(dirs) * len(grid)
+    _check([got[:n0].reshape(len(dirs), -1), got[n0:].reshape(len(dirs), -1)], ref[coherent],
+           1e-10)
+    # host memory is refused (no CPU path)
+    with pytest.raises(R.RadError):
+        R.spectrum_from_sums(total.cpu(), mode, out.cpu())

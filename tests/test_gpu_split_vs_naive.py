@@ -49,18 +49,24 @@ def test_split_phase_keeps_the_upper_decade(workload):
     omega = trajgen.log_grid(0.1, 1000.0, 48)
     wins = [(0, X.shape[0] - 1, 1, 0)]
     ref = oracle.spectra(X, U, w.dt, dirs, [omega], wins, [(N, -1.0)], box_L=w.L)[0]
-    with R.Radiation(dirs, [omega], w.dt, [(N, -1.0, 1.0)], wins, precision=R.RAD_FP32_SPLIT,
-                     box_L=w.L) as r:
-        r.accumulate_steps(0, torch.as_tensor(X, device="cuda"), torch.as_tensor(U, device="cuda"))
-        split = r.finalize()[0]
+    split = {}
+    for name, opts in (("radian", {"variant": R.RAD_VARIANT_SFU, "anchor_K": 32}),
+                       ("turns", {"variant": R.RAD_VARIANT_TURNS, "anchor_K": 32})):
+        with R.Radiation(dirs, [omega], w.dt, [(N, -1.0, 1.0)], wins,
+                         precision=R.RAD_FP32_SPLIT, box_L=w.L, options=opts) as r:
+            r.accumulate_steps(0, torch.as_tensor(X, device="cuda"),
+                               torch.as_tensor(U, device="cuda"))
+            split[name] = r.finalize()[0]
     r_, b_, bd_ = oracle.samples(X, U, w.dt, w.L)
     naive = _naive_fp32_spectrum(r_, b_, bd_, -np.ones(N), w.dt, dirs, omega)
     hi = omega >= 100.0
     for d in range(len(dirs)):
-        e_split = (np.abs(split[d] - ref[d]) / ref[d])[hi].max()
-        e_naive = (np.abs(naive[d] - ref[d]) / ref[d])[hi].max()
-        print(f"workload {workload} dir {d}: max per-bin error, w >= 100: split {e_split:.2e}, "
-              f"naive FP32 {e_naive:.2e}")
-        assert e_split <= 5e-3
-        assert e_naive >= 3 * e_split
-    assert np.linalg.norm(split - ref) <= 1e-4 * np.linalg.norm(ref)
+        e = {k: float((np.abs(v[d] - ref[d]) / ref[d])[hi].max()) for k, v in split.items()}
+        e_naive = float((np.abs(naive[d] - ref[d]) / ref[d])[hi].max())
+        print(f"workload {workload} dir {d}: max per-bin error, w >= 100: split (radian SFU) "
+              f"{e['radian']:.2e}, split (turns) {e['turns']:.2e}, naive FP32 {e_naive:.2e}")
+        assert e["radian"] <= 5e-3
+        assert e["turns"] <= 5e-3
+        assert e_naive >= 3 * e["radian"]
+    for v in split.values():
+        assert np.linalg.norm(v - ref) <= 1e-4 * np.linalg.norm(ref)

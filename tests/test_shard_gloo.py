@@ -28,21 +28,40 @@ def _case():
     return w, X, U, dirs, om
 
 
-def _partial(X, U, w, dirs, om, first, n, coherent):
+def _basis(n):
+    """An orthonormal pair (e1, e2) normal to the unit vector n (any such pair: the
+    coherent spectrum |A|^2 = |A.e1|^2 + |A.e2|^2 because A is normal to n)."""
+    a = np.eye(3)[int(np.argmin(np.abs(n)))]
+    e1 = np.cross(n, a)
+    e1 /= np.linalg.norm(e1)
+    return e1, np.cross(n, e1)
+
+
+def _partial(X, U, w, dirs, om, first, n, coherent, layout="vector"):
+    """A shard's unscaled particle sums: incoherent sum_j |A_j|^2 per bin; coherent
+    sum_j A_j per bin as its 3 complex components ("vector", 6 numbers) or, as
+    rad_partial_sums lays it out, as Re, Im of A.e1 and A.e2 ("basis", 4 numbers)."""
     import oracle
     r, b, bd = oracle.samples(X[:, :, first:first + n], U[:, :, first:first + n], w.dt, w.L)
     if not coherent:
         S = oracle.window_spectrum(r, b, bd, -np.ones(n), w.dt, dirs, om, 0, 120)
         return (S * 4 * math.pi ** 2).reshape(-1)
-    out = np.zeros((len(dirs) * len(om), 6))
+    width = 6 if layout == "vector" else 4
+    out = np.zeros((len(dirs) * len(om), width))
     for d, nv in enumerate(dirs):
+        e1, e2 = _basis(np.asarray(nv) / np.linalg.norm(nv))
         for j in range(n):
             A = oracle.amplitude(r, b, bd, j, 0, 120, w.dt, -1.0, nv, om)   # [nf, 3]
-            out[d * len(om):(d + 1) * len(om)] += np.concatenate([A.real, A.imag], 1)
+            if layout == "vector":
+                part = np.concatenate([A.real, A.imag], 1)
+            else:
+                a1, a2 = A @ e1, A @ e2
+                part = np.stack([a1.real, a1.imag, a2.real, a2.imag], 1)
+            out[d * len(om):(d + 1) * len(om)] += part
     return out
 
 
-def _worker(rank, world, port, coherent, result_q):
+def _worker(rank, world, port, coherent, layout, result_q):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -50,21 +69,23 @@ def _worker(rank, world, port, coherent, result_q):
     from paper_1003_1140_gb300 import shard
     w, X, U, dirs, om = _case()
     first, n = shard.shard(X.shape[2], rank, world)
-    part = _partial(X, U, w, dirs, om, first, n, coherent)
+    part = _partial(X, U, w, dirs, om, first, n, coherent, layout)
     S = shard.allreduce_spectrum(part, coherent)
     if rank == 0:
         result_q.put(S)
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("coherent", [False, True])
-def test_two_rank_shards_reduce_to_the_full_spectrum(coherent):
+@pytest.mark.parametrize("coherent,layout", [(False, "vector"), (True, "vector"),
+                                             (True, "basis")])
+def test_two_rank_shards_reduce_to_the_full_spectrum(coherent, layout):
     import multiprocessing as mp
     import oracle
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, coherent, q)) for r in range(2)]
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, coherent, layout, q))
+             for r in range(2)]
     for p in procs:
         p.start()
     S = q.get(timeout=240)
