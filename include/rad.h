@@ -83,11 +83,6 @@ extern "C" {
 #define RAD_VARIANT_AUTO 0   /* autotuned (or the cached choice) */
 #define RAD_VARIANT_SFU 1    /* every e^{i theta} by the special-function unit */
 #define RAD_VARIANT_MIX 2    /* some frequencies by an FMA-pipe polynomial (see reserved[1]) */
-#define RAD_VARIANT_TURNS 3  /* every e^{i theta} by the special-function unit, the phase
-                                carried in turns and reduced to [-1/2, 1/2] turn first:
-                                the unit's own reduction of a radian argument loses about
-                                1.3e-7 |theta| rad, so at high omega * dphi this variant is
-                                more accurate per frequency bin, for about 3% more time */
 
 typedef struct rad_ctx rad_ctx;
 
@@ -134,7 +129,7 @@ typedef struct {
 
 /* Tuning knobs; zero-initialise for the defaults.  Set before the first step. */
 typedef struct {
-    int32_t variant;       /* RAD_VARIANT_* (AUTO picks among SFU and MIX)   */
+    int32_t variant;       /* RAD_VARIANT_*                                  */
     int32_t anchor_K;      /* FP32 path re-anchor interval: 0 (auto), 8, 16, 32 */
     int32_t freq_per_lane; /* 0 (auto), 8 or 16 frequencies per thread         */
     int32_t defer;         /* 1: evaluate every window in one persistent launch at

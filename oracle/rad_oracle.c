@@ -19,7 +19,7 @@
  *   V         = n x ((n - beta) x betadot) / (1 - n.beta)^2
  *   phi       = t_m - n . r_m / c,      t_m = m dt,   c = 1.
  *
- * Readings of points the paper leaves open (all in the design notes):
+ * Readings of points the paper leaves open (it is silent or garbled on each):
  *   - E_ret of Sec. 2.2 is the Jackson retarded-time integrand V above, and the
  *     garbled phase is phi' = t' - n.r(t')/c.
  *   - the proportionality constant is q^2/(4 pi^2 c) with q inside A.

@@ -37,10 +37,12 @@
 //   chunk of 32 samples x 11 components x 8 particles is one contiguous 11 KB
 //   block (its anchor positions another), staged into shared memory by bulk
 //   TMA copies (cp.async.bulk).  Warp specialisation: a producer warp issues
-//   the copies and turns each chunk into geometry and anchor phases in shared
-//   memory (double-buffered, mbarrier hand-off); eight compute warps run only
-//   the update loop, one particle per warp, FT frequencies per lane (stride
-//   32: coalesced output).
+//   the copies and turns each chunk into geometry and reference phases in
+//   shared memory (double-buffered, mbarrier hand-off); eight compute warps,
+//   one particle per warp, FT frequencies per lane (stride 32: coalesced
+//   output), turn each anchor block's phi_ref into their own anchor phases
+//   (about 12 FP32 operations per frequency per block, so short blocks cost
+//   the compute warps little and the producer nothing) and run the update loop.
 // * Persistent grid with a dynamic longest-first schedule: the producer of each
 //   block takes the next item of a list sorted by decreasing cost from an atomic
 //   counter and describes every chunk it hands over (item, tile, sample range,
@@ -81,6 +83,22 @@ __device__ __forceinline__ void poly_cis_half(float h, float& c2, float& s2half)
     s2half = c * s;
 }
 
+// frac(nu phi_ref) in turns, in [-1, 1]: the float-float product of nu (hi, lo)
+// and phi_ref (hi, lo) with its integer part removed exactly on the FP32 pipe
+// (no round instruction next to the sin/cos of the update loop): adding and
+// removing 1.5 * 2^23 rounds to an integer for |x| < 2^22 and to a float within
+// a few ulp of x above; either difference is exact (Sterbenz), and the second
+// pass brings a large-|x| remainder into [-1/2, 1/2].
+__device__ __forceinline__ float anchor_turns(float nh, float nl, float2 an)
+{
+    const float pr = nh * an.x;
+    const float pe = fmaf(nh, an.x, -pr);
+    const float tl = fmaf(nl, an.x, fmaf(nh, an.y, pe));
+    float fr = pr - ((pr + kMagic) - kMagic);
+    fr = fr - ((fr + kMagic) - kMagic);
+    return fr + tl;
+}
+
 // What the producer tells the compute warps about the chunk in a buffer.
 struct ChunkMeta {
     int64_t out_off;       // the item's output block
@@ -98,8 +116,12 @@ struct Smem32 {
                                                       // a chunk fills comps of the kComps rows)
     float tanc[2][kChunk32 / K][6][kTileP];           // the chunk's anchor positions (hi, lo)
     float4 geo[2][kComputeWarps][kChunk32 + 1];       // V1, V2, dphi per particle and sample
-    float ths[2][kComputeWarps][kChunk32 / K][FT][32];  // anchor phases per particle, block
-    float2 anc[kComputeWarps][kChunk32 / K];          // phi_ref (hi, lo) of the current chunk
+    // the item's nu = w / 2 pi as float-float (hi, lo): lane l's FT values as
+    // FT/4 float4 slots, slot j stored at l * FT/4 + (j ^ ((l >> 2) & 1)) (for
+    // FT = 8 the eight lanes of one 128-bit access phase cover all 32 banks)
+    float4 nu[2][2][32 * FT / 4];
+    float4 nup[2][32 * FT / 4];                       // the producer's copy for the current item
+    float2 anc[2][kComputeWarps][kChunk32 / K];       // phi_ref (hi, lo) per particle, block
     float csh[kComputeWarps][kChunk32 / K];           // centre of each block's offset range
     float red[kComputeWarps][FT][32];                 // window-close partials
     double run[(COH ? 4 : 1) * FT * 32];              // per-item particle sums (FP64)
@@ -160,16 +182,10 @@ struct ChunkCursor {
     }
 };
 
-// TURNS: the phase is carried in turns (nu = w / 2 pi instead of w) and
-// reduced to [-1/2, 1/2] turn before the special-function unit, whose own
-// reduction of a radian argument loses accuracy in proportion to it (about
-// 1.3e-7 |theta| rad measured on GB300; 3.4e-7 rad flat after the reduction),
-// at the cost of three FP32 adds and a multiply per update.  SFU frequencies only.
-template <int FT, int NP, int K, bool COH, int MB, bool TURNS>
+template <int FT, int NP, int K, bool COH, int MB>
 __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum32Params p)
 {
     static_assert(NP >= 0 && NP < FT, "polynomial frequencies per thread");
-    static_assert(!TURNS || NP == 0, "the turns-reduced phase is an SFU variant");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     auto& S = *reinterpret_cast<Smem32<FT, K, COH>*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -200,9 +216,9 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
     // ---------------------------------------------------------------- producer
     // Lane 0 streams the chunks (samples and anchor positions) in with bulk
     // copies one chunk ahead; the whole warp turns each landed chunk into the
-    // per-sample geometry (V1, V2, dphi) and the per-anchor-block phases Theta
-    // of the 8 particles, for the compute warps.  FP32 only: the quantities
-    // that need FP64 accuracy use float-float (error-free) arithmetic.
+    // per-sample geometry (V1, V2, dphi) and the per-anchor-block reference
+    // phases phi_ref of the 8 particles, for the compute warps.  FP32 only: the
+    // quantities that need FP64 accuracy use float-float (error-free) arithmetic.
     if (warp == kComputeWarps) {
         constexpr int NB = kChunk32 / K;                      // anchor blocks per chunk
         constexpr uint32_t kAncBytes = sizeof(S.tanc[0]);
@@ -238,7 +254,6 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
         };
         if (cur.valid) issue(cur, 0);
         int item_loaded = -1;
-        float nuh[FT], nul[FT];
         float n0 = 0, n1 = 0, n2 = 0, e10 = 0, e11 = 0, e12 = 0, e20 = 0, e21 = 0, e22 = 0;
         float nl0 = 0, nl1 = 0, nl2 = 0, qdt = 0;
         int64_t s0 = 0, s1 = 0, out_off = 0;
@@ -270,11 +285,18 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                 row = it.row;
                 tile0 = it.tile0;
 #pragma unroll
-                for (int i = 0; i < FT; ++i) {
-                    const int k = it.ftile * (32 * FT) + lane + 32 * i;
-                    const int kk = w.grid_off + (k < w.grid_len ? k : 0);
-                    nuh[i] = p.nu_hi[kk];
-                    nul[i] = p.nu_lo[kk];
+                for (int j = 0; j < FT / 4; ++j) {
+                    float h[4], l[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int k = it.ftile * (32 * FT) + lane + 32 * (4 * j + q);
+                        const int kk = w.grid_off + (k < w.grid_len ? k : 0);
+                        h[q] = p.nu_hi[kk];
+                        l[q] = p.nu_lo[kk];
+                    }
+                    const int slot = lane * (FT / 4) + (j ^ ((lane >> 2) & 1));
+                    S.nup[0][slot] = make_float4(h[0], h[1], h[2], h[3]);
+                    S.nup[1][slot] = make_float4(l[0], l[1], l[2], l[3]);
                 }
             }
             // after an abort, produce nothing more: the compute warps may still
@@ -334,7 +356,7 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                     e = e + (u.lo - dl);
                 }
                 const float hi = sh + e;
-                S.anc[pp][b] = make_float2(hi, e - (hi - sh));
+                S.anc[buf][pp][b] = make_float2(hi, e - (hi - sh));
             }
             __syncwarp();
             // geometry: round r handles sample 4 r + lane / 8 of particle lane % 8
@@ -376,31 +398,13 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                 S.geo[buf][pp][sm] = make_float4(V1, V2, sh + e, 0.0f);
             }
             __syncwarp();
-            // anchor phases Theta_k = 2 pi frac(nu_k phi_ref) (float-float product,
-            // exact reduction to one turn); halved for the polynomial frequencies
-#pragma unroll 1
-            for (int pp = 0; pp < kTileP; ++pp) {
-#pragma unroll 1
-                for (int b = lo / K; b * K < hi; ++b) {
-                    const float2 an = S.anc[pp][b];
+            // the item's frequencies (nu hi, lo) for the compute warps, which turn
+            // them and the anchors' phi_ref into their anchor phases themselves
 #pragma unroll
-                    for (int i = 0; i < FT; ++i) {
-                        const float pr = nuh[i] * an.x;
-                        const float pe = fmaf(nuh[i], an.x, -pr);
-                        const float tl = fmaf(nul[i], an.x, fmaf(nuh[i], an.y, pe));
-                        // pr minus a nearby integer, on the FP32 pipe (no round
-                        // instruction next to the compute warps' sin/cos): adding
-                        // and removing 1.5 * 2^23 rounds to an integer for
-                        // |pr| < 2^22 and to a float within a few ulp of pr above;
-                        // either difference is exact (Sterbenz), and the second
-                        // pass brings the large-|pr| remainder into [-1/2, 1/2].
-                        float fr = pr - ((pr + kMagic) - kMagic);
-                        fr = fr - ((fr + kMagic) - kMagic);
-                        S.ths[buf][pp][b][i][lane] =
-                            TURNS ? fr + tl
-                                  : (fr + tl) * (i < NS ? 6.28318530717958647f : 3.14159265358979323f);
-                    }
-                }
+            for (int j = 0; j < FT / 4; ++j) {
+                const int slot = lane * (FT / 4) + j;
+                S.nu[buf][0][slot] = S.nup[0][slot];
+                S.nu[buf][1][slot] = S.nup[1][slot];
             }
             if (lane == 0) {
                 ChunkMeta& M = S.meta[buf];
@@ -457,7 +461,7 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
 #pragma unroll
             for (int i = 0; i < FT; ++i) {
                 const int k = it.ftile * (32 * FT) + lane + 32 * i;
-                const float wk = (k < w.grid_len) ? (TURNS ? p.nu_hi : p.omega)[w.grid_off + k] : 0.0f;
+                const float wk = (k < w.grid_len) ? p.omega[w.grid_off + k] : 0.0f;
                 om[i] = (i < NS) ? wk : 0.5f * wk;
             }
         }
@@ -471,23 +475,31 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
         for (int b = lo / K; b * K < hi; ++b) {
             const int l0 = lo > b * K ? lo : b * K;
             const int l1 = hi < b * K + K ? hi : b * K + K;
+            // anchor phases Theta_k = 2 pi frac(nu_k phi_ref): float-float
+            // product, exact reduction to one turn; halved for the polynomial
+            // frequencies
+            const float2 an = S.anc[buf][warp][b];
 #pragma unroll
-            for (int i = 0; i < FT; ++i) th[i] = S.ths[buf][warp][b][i][lane];
+            for (int j = 0; j < FT / 4; ++j) {
+                const int slot = lane * (FT / 4) + (j ^ ((lane >> 2) & 1));
+                const float4 h4 = S.nu[buf][0][slot], l4 = S.nu[buf][1][slot];
+                const float nh[4] = {h4.x, h4.y, h4.z, h4.w}, nl[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int i = 4 * j + q;
+                    th[i] = anchor_turns(nh[q], nl[q], an) *
+                            (i < NS ? 6.28318530717958647f : 3.14159265358979323f);
+                }
+            }
             float4 gg = S.geo[buf][warp][l0];
 #pragma unroll 1
             for (int l = l0; l < l1; ++l) {
                 const float4 gn = S.geo[buf][warp][(l + 1) & (kChunk32 - 1)];
 #pragma unroll
                 for (int i = 0; i < NS; ++i) {
+                    const float tt = fmaf(om[i], gg.z, th[i]);
                     float sn, cs_;
-                    if (TURNS) {
-                        const float t = fmaf(om[i], gg.z, th[i]);
-                        const float r = t - ((t + kMagic) - kMagic);   // exact, |r| <= 1/2
-                        __sincosf(r * 6.28318530717958647f, &sn, &cs_);
-                    } else {
-                        const float tt = fmaf(om[i], gg.z, th[i]);
-                        __sincosf(tt, &sn, &cs_);
-                    }
+                    __sincosf(tt, &sn, &cs_);
                     a1r[i] = fmaf(gg.x, cs_, a1r[i]);
                     a1i[i] = fmaf(gg.x, sn, a1i[i]);
                     a2r[i] = fmaf(gg.y, cs_, a2r[i]);
@@ -579,10 +591,10 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
     }
 }
 
-template <int FT, int NP, int K, bool COH, int MB, bool TURNS = false>
+template <int FT, int NP, int K, bool COH, int MB>
 cudaError_t launch32_one(const Accum32Params& p, int grid, cudaStream_t st)
 {
-    auto kern = accum32_kernel<FT, NP, K, COH, MB, TURNS>;
+    auto kern = accum32_kernel<FT, NP, K, COH, MB>;
     const size_t smem = smem32_bytes<FT, NP, K, COH>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -591,14 +603,14 @@ cudaError_t launch32_one(const Accum32Params& p, int grid, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template <int FT, int NP, int K, bool COH, int MB, bool TURNS = false>
+template <int FT, int NP, int K, bool COH, int MB>
 int blocks32_one()
 {
     int nb = 0;
     const size_t smem = smem32_bytes<FT, NP, K, COH>();
-    if (cudaFuncSetAttribute(accum32_kernel<FT, NP, K, COH, MB, TURNS>,
+    if (cudaFuncSetAttribute(accum32_kernel<FT, NP, K, COH, MB>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, accum32_kernel<FT, NP, K, COH, MB, TURNS>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, accum32_kernel<FT, NP, K, COH, MB>,
                                                       kBlockThreads, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -606,19 +618,11 @@ int blocks32_one()
     return nb;
 }
 
-// One instantiation family: (FT, NP, MB) for every K and both summation modes
-// (radian phase; RAD_ACCUM32_FAMILY_TURNS: the turns-reduced SFU phase).
+// One instantiation family: (FT, NP, MB) for every K and both summation modes.
 #define RAD_ACCUM32_FAMILY(FT, NP, MB)                                                       \
-    if (!cfg.turns && cfg.ft == FT && cfg.np == NP && cfg.mb == MB) {                        \
+    if (cfg.ft == FT && cfg.np == NP && cfg.mb == MB) {                                      \
         if (cfg.K == 8) { if (cfg.coh) FN(FT, NP, 8, true, MB); else FN(FT, NP, 8, false, MB); } \
         if (cfg.K == 16) { if (cfg.coh) FN(FT, NP, 16, true, MB); else FN(FT, NP, 16, false, MB); } \
         if (cfg.K == 32) { if (cfg.coh) FN(FT, NP, 32, true, MB); else FN(FT, NP, 32, false, MB); } \
     }
-#define RAD_ACCUM32_FAMILY_TURNS(FT, MB)                                                     \
-    if (cfg.turns && cfg.ft == FT && cfg.np == 0 && cfg.mb == MB) {                          \
-        if (cfg.K == 8) { if (cfg.coh) FNT(FT, 8, true, MB); else FNT(FT, 8, false, MB); }     \
-        if (cfg.K == 16) { if (cfg.coh) FNT(FT, 16, true, MB); else FNT(FT, 16, false, MB); }  \
-        if (cfg.K == 32) { if (cfg.coh) FNT(FT, 32, true, MB); else FNT(FT, 32, false, MB); }  \
-    }
-
 }  // namespace rad

@@ -271,7 +271,7 @@ bool rad::accum32_dispatch(const Accum32Params* p, const Accum32Config& cfg, int
                            cudaStream_t st, cudaError_t* err, int* nb)
 {
     return accum32_ft8_sfu(p, cfg, grid, st, err, nb) || accum32_ft8_mix(p, cfg, grid, st, err, nb) ||
-           accum32_ft16(p, cfg, grid, st, err, nb) || accum32_ft8_turns(p, cfg, grid, st, err, nb);
+           accum32_ft16(p, cfg, grid, st, err, nb);
 }
 
 static int chunk_len(const rad_ctx* c) { return c->precision == RAD_FP64 ? kChunk64 : kChunk32; }
@@ -371,8 +371,9 @@ static cudaEvent_t next_event(std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& 
 // Largest anchor interval K whose worst-case rounding of the offset phase per
 // update, w_max * |dphi|_max * 2^-24, stays within 1e-4 rad; the offsets are
 // centred in their block, so |dphi| <= (K - 1) dt (1 - n.beta) / 2 <= (K - 1) dt.
-// (The radian SFU variants add the unit's own reduction error, about
-// 1.3e-7 |theta| rad; RAD_VARIANT_TURNS removes it.)
+// (The special-function unit's own reduction of the radian argument adds about
+// 1.3e-7 |theta| rad, and the FP32 roundings of w and dphi add errors of the
+// same order, all proportional to |dphi|.)
 static int budget_K(const rad_ctx* c)
 {
     double wmax = 0.0;
@@ -606,7 +607,6 @@ static int freeze(rad_ctx* c)
         c->cfg.ft = c->opt.freq_per_lane ? c->opt.freq_per_lane : 8;
         c->cfg.np = c->opt.variant == RAD_VARIANT_MIX ? (c->cfg.ft == 8 ? 2 : 4) : 0;
         if (c->opt.variant == RAD_VARIANT_MIX && c->opt.reserved[1] > 0) c->cfg.np = c->opt.reserved[1];
-        c->cfg.turns = c->opt.variant == RAD_VARIANT_TURNS;
         c->cfg.coh = c->mode == RAD_COHERENT;
         c->cfg.mb = c->opt.blocks_per_sm ? c->opt.blocks_per_sm : 2;
         if (c->cfg.ft == 16 && c->cfg.mb != 2)
@@ -1356,10 +1356,7 @@ int rad_set_options(rad_ctx* c, const rad_options* o)
 {
     if (!c || !o) return RAD_EINVAL;
     if (c->frozen) return fail(c, RAD_ESTATE, "options must be set before the first step");
-    if (o->variant < 0 || o->variant > RAD_VARIANT_TURNS)
-        return fail(c, RAD_EINVAL, "variant out of range");
-    if (o->variant == RAD_VARIANT_TURNS && o->freq_per_lane == 16)
-        return fail(c, RAD_EINVAL, "the turns-reduced variant is built for 8 frequencies per thread");
+    if (o->variant < 0 || o->variant > 2) return fail(c, RAD_EINVAL, "variant out of range");
     if (o->anchor_K != 0 && o->anchor_K != 8 && o->anchor_K != 16 && o->anchor_K != 32)
         return fail(c, RAD_EINVAL, "anchor_K must be 0, 8, 16 or 32");
     if (o->freq_per_lane != 0 && o->freq_per_lane != 8 && o->freq_per_lane != 16)
@@ -1444,8 +1441,7 @@ int rad_get_options(const rad_ctx* c, rad_options* o)
         o->anchor_K = c->cfg.K;
         o->freq_per_lane = c->cfg.ft;
         o->blocks_per_sm = c->cfg.mb;
-        o->variant = c->cfg.turns ? RAD_VARIANT_TURNS
-                     : c->cfg.np > 0 ? RAD_VARIANT_MIX : RAD_VARIANT_SFU;
+        o->variant = c->cfg.np > 0 ? RAD_VARIANT_MIX : RAD_VARIANT_SFU;
         o->reserved[1] = c->cfg.np;
     }
     return RAD_OK;

@@ -309,13 +309,11 @@ cudaStream_t ctx_stream(const rad_ctx* c);
 int64_t ctx_particles(const rad_ctx* c);
 int64_t ctx_next_step(const rad_ctx* c);
 // FP32 kernel variant: frequencies per thread, of which np by the FMA-pipe
-// polynomial, anchor interval K, coherent sum, minimum resident blocks per SM,
-// turns-reduced SFU phase.
+// polynomial, anchor interval K, coherent sum, minimum resident blocks per SM.
 struct Accum32Config {
     int ft, np, K;
     bool coh;
     int mb;
-    bool turns = false;
 };
 bool accum32_ft8_sfu(const Accum32Params* p, const Accum32Config& cfg, int grid,
                      cudaStream_t st, cudaError_t* err, int* nb);
@@ -323,8 +321,6 @@ bool accum32_ft8_mix(const Accum32Params* p, const Accum32Config& cfg, int grid,
                      cudaStream_t st, cudaError_t* err, int* nb);
 bool accum32_ft16(const Accum32Params* p, const Accum32Config& cfg, int grid,
                   cudaStream_t st, cudaError_t* err, int* nb);
-bool accum32_ft8_turns(const Accum32Params* p, const Accum32Config& cfg, int grid,
-                       cudaStream_t st, cudaError_t* err, int* nb);
 // launch (p != nullptr) or occupancy query; false if the variant is not built
 bool accum32_dispatch(const Accum32Params* p, const Accum32Config& cfg, int grid,
                       cudaStream_t st, cudaError_t* err, int* nb);

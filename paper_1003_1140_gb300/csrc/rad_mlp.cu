@@ -2,19 +2,21 @@
 // (FP32 master copy), BF16 GEMM operands and FP32 accumulation, trained with
 // MSE and Adam, entirely on the device (C ABI in include/rad_mlp.h).
 //
-// GEMMs run on the 5th-generation tensor cores: one kernel computes
-// C = A B^T for K-contiguous BF16 operands A [M][K], B [N][K].  Per 128 x 128
-// output tile a block of four warps runs a three-stage pipeline:
+// GEMMs run on the 5th-generation tensor cores: one persistent kernel computes
+// C = A B^T for K-contiguous BF16 operands A [M][K], B [N][K], one block of six
+// warps per SM taking 128 x 128 output tiles in turn:
 //   * warp 0, one lane: TMA (cp.async.bulk.tensor.2d) loads of 128 x 64 tiles
-//     of A and B in the 128-byte-swizzled layout, completion on an mbarrier;
+//     of A and B in the 128-byte-swizzled layout into a six-stage ring,
+//     completion on mbarriers;
 //   * warp 1, one lane: four tcgen05.mma (kind::f16, BF16 x BF16 -> FP32,
-//     M 128, N 128, K 16) per stage into a 128-column accumulator in tensor
-//     memory; tcgen05.commit frees the stage and, after the last, signals
-//     the epilogue;
-//   * all four warps: tcgen05.ld of their 32 accumulator rows, a transpose
-//     through shared memory into row-contiguous groups, the fused epilogue
-//     (bias, ReLU, ReLU mask of the backward pass, FP32 and/or BF16 output)
-//     and coalesced global stores.
+//     M 128, N 128, K 16) per stage into one of two 128-column accumulators in
+//     tensor memory (tiles alternate); tcgen05.commit frees the stage and,
+//     after a tile's last stage, hands the accumulator to the epilogue;
+//   * warps 2-5: tcgen05.ld of their 32 accumulator rows, a transpose through
+//     shared memory into row-contiguous groups, the fused epilogue (bias, ReLU,
+//     ReLU mask of the backward pass, FP32 and/or BF16 output) and coalesced
+//     global stores, after which the accumulator goes back to warp 1 -- so a
+//     tile's epilogue overlaps the next tile's loads and MMAs.
 // Products with few output tiles and a long K (the input gradient of the wide
 // output layer: 128 x 512 outputs over K = 393,216) split K across blocks:
 // each slice writes raw FP32 partial sums and one reduction kernel adds the
@@ -45,14 +47,29 @@ typedef __nv_bfloat16 bf16;
 using rad::smem_addr;
 
 constexpr int BM = 128, BN = 128, BK = 64;   // block tile; BK x 2 B = one 128-byte swizzle row
-constexpr int kStages = 3;
-constexpr int kGemmThreads = 128;
+constexpr int kStages = 6;                   // TMA -> MMA pipeline depth
+constexpr int kEpiWarps = 4;                 // epilogue warps (one per 32 TMEM lanes)
+constexpr int kGemmThreads = (2 + kEpiWarps) * 32;   // TMA warp, MMA warp, epilogue warps
 constexpr uint32_t kTileBytes = BM * BK * 2;               // 16 KB per operand per stage
 constexpr uint32_t kStageBytes = 2 * kTileBytes;
-constexpr uint32_t kTmemCols = 128;                        // FP32 accumulator, 128 x 128
-constexpr size_t kGemmSmem = kStages * kStageBytes + 1024 /* alignment */ + 256 /* barriers */;
-constexpr int kSplitTargetBlocks = 2 * 152;  // two resident blocks on each of 152 SMs
+constexpr uint32_t kTmemCols = 2 * BN;                     // two FP32 128 x 128 accumulators
+constexpr size_t kEpiBytes = kEpiWarps * 32 * 32 * sizeof(float);   // transpose staging
+constexpr size_t kGemmSmem = kStages * kStageBytes + kEpiBytes + 1024 /* alignment */ +
+                             256 /* barriers */;
 constexpr int kMinSplitTiles = 4;            // K tiles (of 64) per slice at least
+
+// Streaming multiprocessors of the current device (the persistent GEMM runs one
+// block on each).
+int device_sms()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n;
+}
 
 // tcgen05 instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1),
 // A and B BF16 (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0),
@@ -101,14 +118,14 @@ struct Epilogue {
     int relu;               // apply ReLU before the BF16 store
 };
 
-// Number of K slices for an M x N x K product: enough blocks to fill the GPU
+// Number of K slices for an M x N x K product: enough tiles to fill the GPU
 // twice over when the output alone gives too few, each slice kMinSplitTiles
 // K tiles or more.
 int split_count(int M, int N, int K)
 {
-    const int blocks = (M / BM) * (N / BN), nk = K / BK;
-    if (blocks >= kSplitTargetBlocks / 2) return 1;
-    const int want = (kSplitTargetBlocks + blocks - 1) / blocks;
+    const int blocks = (M / BM) * (N / BN), nk = K / BK, target = 2 * device_sms();
+    if (blocks >= target / 2) return 1;
+    const int want = (target + blocks - 1) / blocks;
     return std::max(1, std::min(want, nk / kMinSplitTiles));
 }
 
@@ -175,33 +192,65 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// C = A B^T over K tiles [kt0, kt1) of slice blockIdx.z; A, B through the
-// tensor maps (K innermost, box 64 x 128, 128-byte swizzle).
-__global__ void __launch_bounds__(kGemmThreads, 2) umma_gemm_kernel(
+// Output tile t of C = A B^T (split into S slices along K): slice z, row tile
+// mi, column tile ni, K tiles [kt0, kt1).  Column tiles vary fastest, so the
+// blocks working at the same time share their A tile in L2.
+struct TileCoord {
+    int z, m0, n0, kt0, kt1;
+};
+
+__device__ __forceinline__ TileCoord tile_coord(int t, int M, int N, int K, int S)
+{
+    const int mt = M / BM, ntl = N / BN, nk_all = K / BK;
+    const int z = t / (mt * ntl), rem = t - z * mt * ntl;
+    TileCoord c;
+    c.z = z;
+    c.m0 = (rem / ntl) * BM;
+    c.n0 = (rem % ntl) * BN;
+    c.kt0 = (int)((int64_t)nk_all * z / S);
+    c.kt1 = (int)((int64_t)nk_all * (z + 1) / S);
+    return c;
+}
+
+// C = A B^T, persistent: block b takes output tiles b, b + gridDim.x, ...
+// Warp 0 (one lane) streams A and B tiles by TMA into a kStages-deep ring of
+// shared-memory stages; warp 1 (one lane) issues the tcgen05 MMAs of a tile
+// into one of two TMEM accumulators and commits it; warps 2-5 drain the other
+// accumulator through the epilogue, so that a tile's epilogue overlaps the
+// next tile's loads and MMAs.  A and B come through the tensor maps (K
+// innermost, box 64 x 128, 128-byte swizzle).  Every wait is bounded: an
+// expired wait raises the block's abort flag and err_word, every role leaves
+// its loop, the TMA warp waits for its loads in flight and the MMA warp for its
+// MMAs before the accumulators are released.
+__global__ void __launch_bounds__(kGemmThreads, 1) umma_gemm_kernel(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M,
-    int N, int K, Epilogue ep, float* partial, int* err_word)
+    int N, int K, int S, Epilogue ep, float* partial, int* err_word)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* full = reinterpret_cast<uint64_t*>(base + kStages * kStageBytes);
+    float* epi = reinterpret_cast<float*>(base + kStages * kStageBytes);
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + kStages * kStageBytes + kEpiBytes);
     uint64_t* empty = full + kStages;
-    uint64_t* accum = empty + kStages;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+    uint64_t* tfull = empty + kStages;    // [2] accumulator b holds a finished tile
+    uint64_t* tempty = tfull + 2;         // [2] accumulator b has been drained
+    uint64_t* mdone = tempty + 2;         // every MMA issued by this block is done
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdone + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
-    const int nk_all = K / BK, S = gridDim.z, z = blockIdx.z;
-    const int kt0 = (int)((int64_t)nk_all * z / S), kt1 = (int)((int64_t)nk_all * (z + 1) / S);
-    const int nk = kt1 - kt0;   // >= 1 (the host keeps every slice non-empty)
+    const int tiles = (M / BM) * (N / BN) * S;
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             rad::mbar_init(&full[s], 1);
             rad::mbar_init(&empty[s], 1);
         }
-        rad::mbar_init(accum, 1);
+        for (int b = 0; b < 2; ++b) {
+            rad::mbar_init(&tfull[b], 1);
+            rad::mbar_init(&tempty[b], kEpiWarps);
+        }
+        rad::mbar_init(mdone, 1);
         *abort_flag = 0;
         rad::fence_mbar_init();
     }
@@ -217,116 +266,144 @@ __global__ void __launch_bounds__(kGemmThreads, 2) umma_gemm_kernel(
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 0 && lane == 0) {
-        // ---- producer: TMA loads, kStages deep
-        int issued = 0;
-        for (int kt = 0; kt < nk; ++kt) {
-            const int s = kt % kStages;
-            const uint32_t u = (uint32_t)(kt / kStages);
-            if (kt >= kStages &&
-                !rad::mbar_wait_bounded(&empty[s], (u - 1) & 1, abort_flag, err_word))
-                break;
-            rad::mbar_arrive_expect_tx(&full[s], kStageBytes);
-            unsigned char* st = base + s * kStageBytes;
-            tma_load_2d(st, &tmA, (kt0 + kt) * BK, m0, &full[s]);
-            tma_load_2d(st + kTileBytes, &tmB, (kt0 + kt) * BK, n0, &full[s]);
-            ++issued;
-        }
-        if (*abort_flag) {
-            // never leave with a copy in flight: wait (bounded) for the last
-            // kStages issued loads to land
-            for (int kt = issued > kStages ? issued - kStages : 0; kt < issued; ++kt)
-                rad::mbar_drain(&full[kt % kStages], (uint32_t)(kt / kStages) & 1);
-        }
-    } else if (warp == 1 && lane == 0) {
-        // ---- MMA issuer
-        bool ok = true;
-        for (int kt = 0; kt < nk && ok; ++kt) {
-            const int s = kt % kStages;
-            const uint32_t u = (uint32_t)(kt / kStages);
-            if (!rad::mbar_wait_bounded(&full[s], u & 1, abort_flag, err_word)) {
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            const uint32_t a0 = smem_addr(base + s * kStageBytes);
-            const uint32_t b0 = a0 + kTileBytes;
-#pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk)
-                umma_bf16(tmem, sw128_desc(a0 + 32 * kk), sw128_desc(b0 + 32 * kk),
-                          (kt > 0 || kk > 0) ? 1u : 0u);
-            umma_commit(&empty[s]);
-        }
-        // the accumulator barrier completes once every MMA issued above is done
-        // (also after an abort, so the epilogue's drain below always ends)
-        umma_commit(accum);
-    }
-    __syncwarp();
-
-    // ---- epilogue: warp w owns accumulator rows (TMEM lanes) 32 w .. 32 w + 31.
-    // Each 32 x 32 block goes TMEM -> registers (one row per lane) -> shared
-    // memory (the drained pipeline buffers; float4 slots XOR-swizzled by row,
-    // conflict-free both ways) -> registers (four consecutive columns per
-    // lane, eight lanes per row), so every global access of a warp covers four
-    // whole 128-byte row segments.
-    const bool ready = rad::mbar_wait_bounded(accum, 0, abort_flag, err_word);
-    if (!ready) rad::mbar_drain(accum, 0);
-    __syncwarp();     // tcgen05.ld below is warp-collective
-    tc_fence_after();
-    const bool live = ready && !*abort_flag;
-    float* stage = reinterpret_cast<float*>(base) + warp * 32 * 32;
-    const int qi = lane & 7, ri = lane >> 3;
-#pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-        float4* srow = reinterpret_cast<float4*>(stage + lane * 32);
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            srow[j ^ (lane & 7)] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-        __syncwarp();
-        if (live) {
-#pragma unroll 2
-            for (int k = 0; k < 8; ++k) {
-                const int r = 4 * k + ri;
-                float4 x = reinterpret_cast<const float4*>(stage + r * 32)[qi ^ (r & 7)];
-                const int n = n0 + c0 + 4 * qi;
-                const size_t o = (size_t)(m0 + warp * 32 + r) * N + n;
-                if (partial) {
-                    *reinterpret_cast<float4*>(partial + (size_t)z * M * N + o) = x;
-                    continue;
-                }
-                if (ep.bias) {
-                    const float4 b = *reinterpret_cast<const float4*>(ep.bias + n);
-                    x.x += b.x;
-                    x.y += b.y;
-                    x.z += b.z;
-                    x.w += b.w;
-                }
-                if (ep.mask) {
-                    const float4 q = *reinterpret_cast<const float4*>(ep.mask + o);
-                    x.x = q.x > 0.0f ? x.x : 0.0f;
-                    x.y = q.y > 0.0f ? x.y : 0.0f;
-                    x.z = q.z > 0.0f ? x.z : 0.0f;
-                    x.w = q.w > 0.0f ? x.w : 0.0f;
-                }
-                if (ep.out_f32) *reinterpret_cast<float4*>(ep.out_f32 + o) = x;
-                if (ep.out_bf16) {
-                    if (ep.relu) {
-                        x.x = fmaxf(x.x, 0.0f);
-                        x.y = fmaxf(x.y, 0.0f);
-                        x.z = fmaxf(x.z, 0.0f);
-                        x.w = fmaxf(x.w, 0.0f);
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- TMA producer: stage use counter `it` runs across tiles
+            uint32_t it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+                const TileCoord tc = tile_coord(t, M, N, K, S);
+                for (int kt = tc.kt0; kt < tc.kt1; ++kt, ++it) {
+                    const int s = (int)(it % kStages);
+                    const uint32_t u = it / kStages;
+                    if (it >= (uint32_t)kStages &&
+                        !rad::mbar_wait_bounded(&empty[s], (u - 1) & 1, abort_flag, err_word)) {
+                        ok = false;
+                        break;
                     }
-                    const __nv_bfloat162 lo = __floats2bfloat162_rn(x.x, x.y);
-                    const __nv_bfloat162 hi = __floats2bfloat162_rn(x.z, x.w);
-                    *reinterpret_cast<uint2*>(ep.out_bf16 + o) =
-                        make_uint2(*reinterpret_cast<const uint32_t*>(&lo),
-                                   *reinterpret_cast<const uint32_t*>(&hi));
+                    rad::mbar_arrive_expect_tx(&full[s], kStageBytes);
+                    unsigned char* st = base + s * kStageBytes;
+                    tma_load_2d(st, &tmA, kt * BK, tc.m0, &full[s]);
+                    tma_load_2d(st + kTileBytes, &tmB, kt * BK, tc.n0, &full[s]);
                 }
             }
+            if (!ok || *abort_flag) {
+                // never leave with a copy in flight: wait (bounded) for the last
+                // kStages issued loads to land
+                for (uint32_t j = it > (uint32_t)kStages ? it - kStages : 0; j < it; ++j)
+                    rad::mbar_drain(&full[j % kStages], (j / kStages) & 1);
+            }
         }
-        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer: tile i of this block goes to accumulator i & 1
+            uint32_t it = 0, i = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++i) {
+                const TileCoord tc = tile_coord(t, M, N, K, S);
+                const int ab = (int)(i & 1);
+                const uint32_t use = i >> 1;
+                if (use >= 1 &&
+                    !rad::mbar_wait_bounded(&tempty[ab], (use - 1) & 1, abort_flag, err_word))
+                    break;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(ab * BN);
+                for (int kt = tc.kt0; kt < tc.kt1; ++kt, ++it) {
+                    const int s = (int)(it % kStages);
+                    const uint32_t u = it / kStages;
+                    if (!rad::mbar_wait_bounded(&full[s], u & 1, abort_flag, err_word)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_addr(base + s * kStageBytes);
+                    const uint32_t b0 = a0 + kTileBytes;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk)
+                        umma_bf16(d, sw128_desc(a0 + 32 * kk), sw128_desc(b0 + 32 * kk),
+                                  (kt > tc.kt0 || kk > 0) ? 1u : 0u);
+                    umma_commit(&empty[s]);
+                }
+                if (ok) umma_commit(&tfull[ab]);
+            }
+            // completes once every MMA issued above is done (also after an abort)
+            umma_commit(mdone);
+            rad::mbar_drain(mdone, 0);
+        }
+    } else {
+        // ---- epilogue: warp w may read TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31,
+        // the accumulator rows of that quarter.  Each 32 x 32 block goes TMEM ->
+        // registers (one row per lane) -> this warp's staging (float4 slots
+        // XOR-swizzled by row, conflict-free both ways) -> registers (four
+        // consecutive columns per lane, eight lanes per row), so every global
+        // access of a warp covers four whole 128-byte row segments.
+        const int lg = warp & 3;
+        float* stage = epi + (warp - 2) * 32 * 32;
+        const int qi = lane & 7, ri = lane >> 3;
+        uint32_t i = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+            const TileCoord tc = tile_coord(t, M, N, K, S);
+            const int ab = (int)(i & 1);
+            const bool ready = rad::mbar_wait_bounded(&tfull[ab], (i >> 1) & 1, abort_flag, err_word);
+            // tcgen05.ld below is warp-collective: the whole warp goes on or stops
+            if (!__all_sync(0xffffffffu, ready && !*abort_flag)) break;
+            tc_fence_after();
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(ab * BN + c0), v);
+                float4* srow = reinterpret_cast<float4*>(stage + lane * 32);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    srow[j ^ (lane & 7)] =
+                        make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                __syncwarp();
+#pragma unroll 2
+                for (int k = 0; k < 8; ++k) {
+                    const int r = 4 * k + ri;
+                    float4 x = reinterpret_cast<const float4*>(stage + r * 32)[qi ^ (r & 7)];
+                    const int n = tc.n0 + c0 + 4 * qi;
+                    const size_t o = (size_t)(tc.m0 + lg * 32 + r) * N + n;
+                    if (partial) {
+                        *reinterpret_cast<float4*>(partial + (size_t)tc.z * M * N + o) = x;
+                        continue;
+                    }
+                    if (ep.bias) {
+                        const float4 b = *reinterpret_cast<const float4*>(ep.bias + n);
+                        x.x += b.x;
+                        x.y += b.y;
+                        x.z += b.z;
+                        x.w += b.w;
+                    }
+                    if (ep.mask) {
+                        const float4 q = *reinterpret_cast<const float4*>(ep.mask + o);
+                        x.x = q.x > 0.0f ? x.x : 0.0f;
+                        x.y = q.y > 0.0f ? x.y : 0.0f;
+                        x.z = q.z > 0.0f ? x.z : 0.0f;
+                        x.w = q.w > 0.0f ? x.w : 0.0f;
+                    }
+                    if (ep.out_f32) *reinterpret_cast<float4*>(ep.out_f32 + o) = x;
+                    if (ep.out_bf16) {
+                        if (ep.relu) {
+                            x.x = fmaxf(x.x, 0.0f);
+                            x.y = fmaxf(x.y, 0.0f);
+                            x.z = fmaxf(x.z, 0.0f);
+                            x.w = fmaxf(x.w, 0.0f);
+                        }
+                        const __nv_bfloat162 lo = __floats2bfloat162_rn(x.x, x.y);
+                        const __nv_bfloat162 hi = __floats2bfloat162_rn(x.z, x.w);
+                        *reinterpret_cast<uint2*>(ep.out_bf16 + o) =
+                            make_uint2(*reinterpret_cast<const uint32_t*>(&lo),
+                                       *reinterpret_cast<const uint32_t*>(&hi));
+                    }
+                }
+                __syncwarp();
+            }
+            // this warp's reads of the accumulator are complete: hand it back
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) rad::mbar_arrive(&tempty[ab]);
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -456,12 +533,12 @@ cudaError_t gemm_tn(const bf16* A, int lda, const bf16* B, int ldb, int M, int N
         return cudaErrorInvalidValue;
     }
     const int S = work ? split_count(M, N, K) : 1;
-    dim3 grid(N / BN, M / BM, S);
-    umma_gemm_kernel<<<grid, kGemmThreads, kGemmSmem, st>>>(ma, mb, M, N, K, ep,
-                                                           S > 1 ? work : nullptr, err_word);
+    const int tiles = (M / BM) * (N / BN) * S, sms = device_sms();
+    umma_gemm_kernel<<<std::min(tiles, sms), kGemmThreads, kGemmSmem, st>>>(
+        ma, mb, M, N, K, S, ep, S > 1 ? work : nullptr, err_word);
     if (S > 1) {
         const int64_t n4 = (int64_t)M * N / 4;
-        const int blocks = (int)std::min<int64_t>((n4 + 255) / 256, 4 * 152);
+        const int blocks = (int)std::min<int64_t>((n4 + 255) / 256, 4 * sms);
         splitk_reduce<<<blocks, 256, 0, st>>>(work, S, M, N, ep);
     }
     e = cudaGetLastError();

@@ -50,8 +50,8 @@ def test_split_phase_keeps_the_upper_decade(workload):
     wins = [(0, X.shape[0] - 1, 1, 0)]
     ref = oracle.spectra(X, U, w.dt, dirs, [omega], wins, [(N, -1.0)], box_L=w.L)[0]
     split = {}
-    for name, opts in (("radian", {"variant": R.RAD_VARIANT_SFU, "anchor_K": 32}),
-                       ("turns", {"variant": R.RAD_VARIANT_TURNS, "anchor_K": 32})):
+    for name, opts in (("K32", {"variant": R.RAD_VARIANT_SFU, "anchor_K": 32}),
+                       ("K8", {"variant": R.RAD_VARIANT_SFU, "anchor_K": 8})):
         with R.Radiation(dirs, [omega], w.dt, [(N, -1.0, 1.0)], wins,
                          precision=R.RAD_FP32_SPLIT, box_L=w.L, options=opts) as r:
             r.accumulate_steps(0, torch.as_tensor(X, device="cuda"),
@@ -63,10 +63,10 @@ def test_split_phase_keeps_the_upper_decade(workload):
     for d in range(len(dirs)):
         e = {k: float((np.abs(v[d] - ref[d]) / ref[d])[hi].max()) for k, v in split.items()}
         e_naive = float((np.abs(naive[d] - ref[d]) / ref[d])[hi].max())
-        print(f"workload {workload} dir {d}: max per-bin error, w >= 100: split (radian SFU) "
-              f"{e['radian']:.2e}, split (turns) {e['turns']:.2e}, naive FP32 {e_naive:.2e}")
-        assert e["radian"] <= 5e-3
-        assert e["turns"] <= 5e-3
-        assert e_naive >= 3 * e["radian"]
+        print(f"workload {workload} dir {d}: max per-bin error, w >= 100: split K = 32 "
+              f"{e['K32']:.2e}, split K = 8 {e['K8']:.2e}, naive FP32 {e_naive:.2e}")
+        assert e["K32"] <= 5e-3
+        assert e["K8"] <= 1e-3
+        assert e_naive >= 3 * e["K32"]
     for v in split.values():
         assert np.linalg.norm(v - ref) <= 1e-4 * np.linalg.norm(ref)
