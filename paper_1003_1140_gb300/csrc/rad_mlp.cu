@@ -3,20 +3,21 @@
 // MSE and Adam, entirely on the device (C ABI in include/rad_mlp.h).
 //
 // GEMMs run on the 5th-generation tensor cores: one persistent kernel computes
-// C = A B^T for K-contiguous BF16 operands A [M][K], B [N][K], one block of six
+// C = A B^T for K-contiguous BF16 operands A [M][K], B [N][K], one block of ten
 // warps per SM taking 128 x 128 output tiles in turn:
 //   * warp 0, one lane: TMA (cp.async.bulk.tensor.2d) loads of 128 x 64 tiles
-//     of A and B in the 128-byte-swizzled layout into a six-stage ring,
+//     of A and B in the 128-byte-swizzled layout into a five-stage ring,
 //     completion on mbarriers;
 //   * warp 1, one lane: four tcgen05.mma (kind::f16, BF16 x BF16 -> FP32,
 //     M 128, N 128, K 16) per stage into one of two 128-column accumulators in
 //     tensor memory (tiles alternate); tcgen05.commit frees the stage and,
 //     after a tile's last stage, hands the accumulator to the epilogue;
-//   * warps 2-5: tcgen05.ld of their 32 accumulator rows, a transpose through
-//     shared memory into row-contiguous groups, the fused epilogue (bias, ReLU,
-//     ReLU mask of the backward pass, FP32 and/or BF16 output) and coalesced
-//     global stores, after which the accumulator goes back to warp 1 -- so a
-//     tile's epilogue overlaps the next tile's loads and MMAs.
+//   * warps 2-9: tcgen05.ld of 32 accumulator rows x 64 columns each, a
+//     transpose through shared memory into row-contiguous groups, the fused
+//     epilogue (bias, ReLU, ReLU mask of the backward pass, FP32 and/or BF16
+//     output) and coalesced global stores, after which the accumulator goes
+//     back to warp 1 -- so a tile's epilogue overlaps the next tile's loads
+//     and MMAs.
 // Products with few output tiles and a long K (the input gradient of the wide
 // output layer: 128 x 512 outputs over K = 393,216) split K across blocks:
 // each slice writes raw FP32 partial sums and one reduction kernel adds the
@@ -47,8 +48,9 @@ typedef __nv_bfloat16 bf16;
 using rad::smem_addr;
 
 constexpr int BM = 128, BN = 128, BK = 64;   // block tile; BK x 2 B = one 128-byte swizzle row
-constexpr int kStages = 6;                   // TMA -> MMA pipeline depth
-constexpr int kEpiWarps = 4;                 // epilogue warps (one per 32 TMEM lanes)
+constexpr int kStages = 5;                   // TMA -> MMA pipeline depth
+constexpr int kEpiWarps = 8;                 // epilogue warps: two per 32 TMEM lanes, each
+                                             // storing half of the tile's columns
 constexpr int kGemmThreads = (2 + kEpiWarps) * 32;   // TMA warp, MMA warp, epilogue warps
 constexpr uint32_t kTileBytes = BM * BK * 2;               // 16 KB per operand per stage
 constexpr uint32_t kStageBytes = 2 * kTileBytes;
@@ -215,9 +217,9 @@ __device__ __forceinline__ TileCoord tile_coord(int t, int M, int N, int K, int 
 // C = A B^T, persistent: block b takes output tiles b, b + gridDim.x, ...
 // Warp 0 (one lane) streams A and B tiles by TMA into a kStages-deep ring of
 // shared-memory stages; warp 1 (one lane) issues the tcgen05 MMAs of a tile
-// into one of two TMEM accumulators and commits it; warps 2-5 drain the other
-// accumulator through the epilogue, so that a tile's epilogue overlaps the
-// next tile's loads and MMAs.  A and B come through the tensor maps (K
+// into one of two TMEM accumulators and commits it; warps 2-9 drain the other
+// accumulator through the epilogue (two warps per 32-row quarter, 64 columns
+// each), so that a tile's epilogue overlaps the next tile's loads and MMAs.  A and B come through the tensor maps (K
 // innermost, box 64 x 128, 128-byte swizzle).  Every wait is bounded: an
 // expired wait raises the block's abort flag and err_word, every role leaves
 // its loop, the TMA warp waits for its loads in flight and the MMA warp for its
@@ -332,12 +334,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1) umma_gemm_kernel(
         }
     } else {
         // ---- epilogue: warp w may read TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31,
-        // the accumulator rows of that quarter.  Each 32 x 32 block goes TMEM ->
+        // the accumulator rows of that quarter; warps 2-5 take columns 0-63 and
+        // warps 6-9 columns 64-127.  Each 32 x 32 block goes TMEM ->
         // registers (one row per lane) -> this warp's staging (float4 slots
         // XOR-swizzled by row, conflict-free both ways) -> registers (four
         // consecutive columns per lane, eight lanes per row), so every global
         // access of a warp covers four whole 128-byte row segments.
-        const int lg = warp & 3;
+        const int lg = warp & 3, cbase = ((warp - 2) >> 2) * (BN / 2);
         float* stage = epi + (warp - 2) * 32 * 32;
         const int qi = lane & 7, ri = lane >> 3;
         uint32_t i = 0;
@@ -349,7 +352,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) umma_gemm_kernel(
             if (!__all_sync(0xffffffffu, ready && !*abort_flag)) break;
             tc_fence_after();
 #pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 32) {
+            for (int c0 = cbase; c0 < cbase + BN / 2; c0 += 32) {
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(ab * BN + c0), v);
                 float4* srow = reinterpret_cast<float4*>(stage + lane * 32);
