@@ -42,12 +42,12 @@ if ROOT not in sys.path:
 
 METRIC = "G particle·step·ω·n updates/s, FP32 split vs FP64 GPU at ≤1e-4 rel L2"
 
-# DRAM bytes (read + write) of one accumulation launch from an ncu capture
-# (particles: the captured launch's particle count, with this workload's samples,
-# directions and omegas), valid while the code (comments aside) of the kernel and of
-# its work-list builder is the code that was captured; traffic scales with the
-# particle count.  None: no capture of the current code.
-TRAFFIC_CAPTURE = None
+# DRAM bytes (read + write) of one accumulation launch from an ncu capture of this
+# workload scaled to 4096 particles (same samples, directions and omegas), valid while
+# the code (comments aside) of the kernel and of its work-list builder is the code that
+# was captured; traffic scales with the particle count.
+TRAFFIC_CAPTURE = {"sources_sha256": "10fc1b54d64fc32862f170357b44e71c81758ebb54752739a8a96edc90ba6d64",
+                   "bytes_per_launch": 696.830464e6, "particles": 4096}
 UNIT = "G updates/s"
 WORKLOAD = 3
 # device memory kept free beside the resident trajectory and one shard's ring

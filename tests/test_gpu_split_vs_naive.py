@@ -1,17 +1,20 @@
-"""Why the FP32 path splits the phase.  On the relative-L2 target (1e-4 per
-direction) even a naive FP32 phase -- theta = w (t - n.r) rounded to single
-precision, no anchors -- would pass on the bench workload, because the power
-sits at low frequency where w ulp(phi) is small.  In the upper decade
-(w >= 100, phases up to w phi ~ 1e5 rad) the naive phase is off by up to
-1-2% per bin.  The split path (FP64-class anchors, FP32 offsets of at most
-K/2 samples, K = 32) keeps the offset phase below ~1600 rad, where FP32
-rounding is ~1e-4 rad per sample: its worst upper-decade bins are ~1e-3 off,
-4 to 12 times better than the naive phase (measured: 1.8e-3 vs 1.6e-2 and
-4.1e-4 vs 5.0e-3 at gamma 3, 1.0e-3 vs 1.1e-2 and 5.5e-4 vs 2.4e-3 at
-gamma 10).  Both are measured against the FP64 oracle on the first
-4 particles of the bench workload (gamma 3) and of the precision workload
-(gamma 10); the naive variant is evaluated here from the oracle's FP64
-samples, with V and the sums in FP64 so that only the phase differs."""
+"""Why the FP32 path splits the phase, and what the anchor interval K buys.
+On the relative-L2 target (1e-4 per direction) even a naive FP32 phase --
+theta = w (t - n.r) rounded to single precision, no anchors -- would pass on
+these workloads, because the power sits at low frequency where w ulp(phi) is
+small.  In the upper decade (w >= 100, phases up to w phi ~ 1e5 rad) the naive
+phase is off by up to 1-2% per bin.  The split path (FP64-class anchors, FP32
+offsets centred in their anchor block, |dphi| <= (K - 1) dt (1 - n.beta) / 2)
+keeps the offset phase below ~800 rad at K = 32 and ~200 rad at K = 8; its
+errors (the FP32 roundings of w, dphi and theta and the special-function
+unit's reduction of the radian argument) grow with w |dphi|, so the worst
+upper-decade bin falls with K (measured on GB300 for this test's +x direction at
+gamma 3: 4.4e-4 at K = 32 and 1.6e-4 at K = 8, against 1.6e-2 for the naive
+phase).  All three are
+measured against the FP64 oracle on the first 4 particles of the FP64-at-scale
+workload (gamma 3) and of the precision workload (gamma 10); the naive variant
+is evaluated here from the oracle's FP64 samples, with V and the sums in FP64
+so that only the phase differs."""
 import numpy as np
 import pytest
 
