@@ -131,15 +131,16 @@ typedef struct {
 typedef struct {
     int32_t variant;       /* RAD_VARIANT_*                                  */
     int32_t anchor_K;      /* FP32 path re-anchor interval: 0 (auto), 8, 16, 32 */
-    int32_t freq_per_lane; /* 0 (auto), 8 or 16 frequencies per thread         */
+    int32_t freq_per_lane; /* 0 (auto), 4, 8 or 16 frequencies per thread      */
     int32_t defer;         /* 1: evaluate every window in one persistent launch at
                               finalize instead of when its last sample arrives */
     int32_t use_graph;     /* 1: FP32 path, one step per call, device inputs: replay
                               each step's launches (ingest; at a closing step also
                               the accumulation) as an instantiated CUDA graph    */
     int32_t check_inputs;  /* 1: flag non-finite x/u (RAD_ENAN at finalize)    */
-    int32_t blocks_per_sm; /* 0 (auto), 2 or 3: resident blocks per SM the FP32
-                              kernel is built for (its register budget)    */
+    int32_t blocks_per_sm; /* 0 (auto), 2, 3 or 4: resident blocks per SM the FP32
+                              kernel is built for (its register budget); 4
+                              frequencies per thread go with 4, 16 with 2    */
     int32_t subcycle;      /* 0 or 1: none; n >= 2: n sub-samples per PIC sample
                               (Sec. 2.2 sub-cycling of the tracked particles):
                               u linear in time between the half-step states,

@@ -99,6 +99,16 @@ __device__ __forceinline__ float anchor_turns(float nh, float nl, float2 an)
     return fr + tl;
 }
 
+// Shared-memory slot of lane l's j-th float4 of frequencies: l * FT/4 + j, with j
+// flipped for every other group of four lanes when a lane has two or more slots,
+// so that the eight lanes of one 128-bit access phase cover all 32 banks.
+template <int FT>
+__device__ __forceinline__ int nu_slot(int lane, int j)
+{
+    static_assert(FT % 4 == 0, "frequencies per thread come in float4 slots");
+    return lane * (FT / 4) + (FT / 4 > 1 ? (j ^ ((lane >> 2) & 1)) : j);
+}
+
 // What the producer tells the compute warps about the chunk in a buffer.
 struct ChunkMeta {
     int64_t out_off;       // the item's output block
@@ -117,8 +127,7 @@ struct Smem32 {
     float tanc[2][kChunk32 / K][6][kTileP];           // the chunk's anchor positions (hi, lo)
     float4 geo[2][kComputeWarps][kChunk32 + 1];       // V1, V2, dphi per particle and sample
     // the item's nu = w / 2 pi as float-float (hi, lo): lane l's FT values as
-    // FT/4 float4 slots, slot j stored at l * FT/4 + (j ^ ((l >> 2) & 1)) (for
-    // FT = 8 the eight lanes of one 128-bit access phase cover all 32 banks)
+    // FT/4 float4 slots at nu_slot<FT>(l, j)
     float4 nu[2][2][32 * FT / 4];
     float4 nup[2][32 * FT / 4];                       // the producer's copy for the current item
     float2 anc[2][kComputeWarps][kChunk32 / K];       // phi_ref (hi, lo) per particle, block
@@ -294,7 +303,7 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                         h[q] = p.nu_hi[kk];
                         l[q] = p.nu_lo[kk];
                     }
-                    const int slot = lane * (FT / 4) + (j ^ ((lane >> 2) & 1));
+                    const int slot = nu_slot<FT>(lane, j);
                     S.nup[0][slot] = make_float4(h[0], h[1], h[2], h[3]);
                     S.nup[1][slot] = make_float4(l[0], l[1], l[2], l[3]);
                 }
@@ -481,7 +490,7 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
             const float2 an = S.anc[buf][warp][b];
 #pragma unroll
             for (int j = 0; j < FT / 4; ++j) {
-                const int slot = lane * (FT / 4) + (j ^ ((lane >> 2) & 1));
+                const int slot = nu_slot<FT>(lane, j);
                 const float4 h4 = S.nu[buf][0][slot], l4 = S.nu[buf][1][slot];
                 const float nh[4] = {h4.x, h4.y, h4.z, h4.w}, nl[4] = {l4.x, l4.y, l4.z, l4.w};
 #pragma unroll

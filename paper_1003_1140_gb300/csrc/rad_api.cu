@@ -271,7 +271,7 @@ bool rad::accum32_dispatch(const Accum32Params* p, const Accum32Config& cfg, int
                            cudaStream_t st, cudaError_t* err, int* nb)
 {
     return accum32_ft8_sfu(p, cfg, grid, st, err, nb) || accum32_ft8_mix(p, cfg, grid, st, err, nb) ||
-           accum32_ft16(p, cfg, grid, st, err, nb);
+           accum32_ft16(p, cfg, grid, st, err, nb) || accum32_ft4(p, cfg, grid, st, err, nb);
 }
 
 static int chunk_len(const rad_ctx* c) { return c->precision == RAD_FP64 ? kChunk64 : kChunk32; }
@@ -497,7 +497,7 @@ static int autotune32(rad_ctx* c, int K)
     }
     const bool coh = c->mode == RAD_COHERENT;
     std::vector<Accum32Config> cands = {{8, 0, K, coh, 2}, {8, 0, K, coh, 3}, {8, 1, K, coh, 2},
-                                        {8, 1, K, coh, 3}, {8, 2, K, coh, 2}};
+                                        {8, 1, K, coh, 3}, {8, 2, K, coh, 2}, {4, 0, K, coh, 4}};
     // small problems: not worth timing
     if (rad_updates(c) < (int64_t)2e10) {
         c->cfg = cands[0];
@@ -549,9 +549,10 @@ static int autotune32(rad_ctx* c, int K)
             CU(cudaEventSynchronize(e1));
             float ms = 0;
             CU(cudaEventElapsedTime(&ms, e0, e1));
-            // per item (the items are alike), so candidates with different
-            // numbers of resident blocks compare fairly
-            ms_min = std::min(ms_min, ms / (float)n);
+            // per particle tile x frequency (an item covers 32 ft frequencies of one
+            // tile), so candidates with different item sizes and numbers of
+            // resident blocks compare fairly
+            ms_min = std::min(ms_min, ms / ((float)n * (float)cand.ft));
         }
         cudaFree(d_items);
         if (ms_min < best_ms) {
@@ -611,6 +612,10 @@ static int freeze(rad_ctx* c)
         c->cfg.mb = c->opt.blocks_per_sm ? c->opt.blocks_per_sm : 2;
         if (c->cfg.ft == 16 && c->cfg.mb != 2)
             return fail(c, RAD_EINVAL, "16 frequencies per thread is built for 2 blocks per SM only");
+        if (c->cfg.ft == 4 && (c->cfg.mb != 4 || c->cfg.np != 0))
+            return fail(c, RAD_EINVAL, "4 frequencies per thread is built for 4 blocks per SM, SFU only");
+        if (c->cfg.ft == 8 && c->cfg.mb == 4)
+            return fail(c, RAD_EINVAL, "8 frequencies per thread is built for 2 or 3 blocks per SM");
         const bool tune = c->opt.variant == RAD_VARIANT_AUTO && !c->opt.freq_per_lane &&
                           !c->opt.blocks_per_sm;
         if (!c->opt.anchor_K && tune) {
@@ -1359,12 +1364,14 @@ int rad_set_options(rad_ctx* c, const rad_options* o)
     if (o->variant < 0 || o->variant > 2) return fail(c, RAD_EINVAL, "variant out of range");
     if (o->anchor_K != 0 && o->anchor_K != 8 && o->anchor_K != 16 && o->anchor_K != 32)
         return fail(c, RAD_EINVAL, "anchor_K must be 0, 8, 16 or 32");
-    if (o->freq_per_lane != 0 && o->freq_per_lane != 8 && o->freq_per_lane != 16)
-        return fail(c, RAD_EINVAL, "freq_per_lane must be 0, 8 or 16");
+    if (o->freq_per_lane != 0 && o->freq_per_lane != 4 && o->freq_per_lane != 8 &&
+        o->freq_per_lane != 16)
+        return fail(c, RAD_EINVAL, "freq_per_lane must be 0, 4, 8 or 16");
     if (o->subcycle < 0 || o->subcycle > 64)
         return fail(c, RAD_EINVAL, "subcycle must be in [0, 64]");
-    if (o->blocks_per_sm != 0 && o->blocks_per_sm != 2 && o->blocks_per_sm != 3)
-        return fail(c, RAD_EINVAL, "blocks_per_sm must be 0, 2 or 3");
+    if (o->blocks_per_sm != 0 && o->blocks_per_sm != 2 && o->blocks_per_sm != 3 &&
+        o->blocks_per_sm != 4)
+        return fail(c, RAD_EINVAL, "blocks_per_sm must be 0, 2, 3 or 4");
     c->opt = *o;
     c->time_ingest = o->reserved[0] != 0;
     return RAD_OK;

@@ -321,6 +321,8 @@ bool accum32_ft8_mix(const Accum32Params* p, const Accum32Config& cfg, int grid,
                      cudaStream_t st, cudaError_t* err, int* nb);
 bool accum32_ft16(const Accum32Params* p, const Accum32Config& cfg, int grid,
                   cudaStream_t st, cudaError_t* err, int* nb);
+bool accum32_ft4(const Accum32Params* p, const Accum32Config& cfg, int grid,
+                 cudaStream_t st, cudaError_t* err, int* nb);
 // launch (p != nullptr) or occupancy query; false if the variant is not built
 bool accum32_dispatch(const Accum32Params* p, const Accum32Config& cfg, int grid,
                       cudaStream_t st, cudaError_t* err, int* nb);

@@ -97,11 +97,11 @@ def test_fp32_split_matches_oracle(two_species, coherent, K):
 
 
 @pytest.mark.parametrize("variant,ft,mb", [(1, 16, 2), (1, 8, 3), (2, 8, 2), (2, 8, 3),
-                                           (2, 16, 2)])
+                                           (2, 16, 2), (1, 4, 4)])
 @pytest.mark.parametrize("coherent", [False, True])
 def test_fp32_split_kernel_variants(two_species, variant, ft, mb, coherent):
-    """SFU-only and SFU + FMA-polynomial (MIX) kernels, 8 or 16 frequencies per
-    thread, built for 2 or 3 resident blocks per SM."""
+    """SFU-only and SFU + FMA-polynomial (MIX) kernels, 4, 8 or 16 frequencies per
+    thread, built for 2, 3 or 4 resident blocks per SM."""
     R = _rad()
     w, X, U, ref = two_species
     got = _run(w, X, U, R.RAD_FP32_SPLIT, coherent,

@@ -159,3 +159,50 @@ def test_spectrum_from_summed_partials_on_the_device(sharded, coherent):
     # host memory is refused (no CPU path)
     with pytest.raises(R.RadError):
         R.spectrum_from_sums(total.cpu(), mode, out.cpu())
+
+
+def test_direction_sets_through_every_path():
+    """Windows with direction subsets through each way the library takes inputs: device
+    inputs in one batch, host inputs through the particle-blocked transfer (2048 particles,
+    blocks of whole tiles with their own work lists), one call per step replayed as CUDA
+    graphs, deferred windows, and two particle shards -- all against the oracle, and with
+    each other up to the order of the FP64 sums."""
+    R = _rad()
+    w = trajgen.config(2, 2048 / 65536)
+    X, U = w.trajectory_numpy(n_calls=129)
+    N = X.shape[2]
+    grids = [trajgen.log_grid(0.1, 300.0, 64)]
+    wins = [(0, 128, 1, 0, [6, 0, 2]), (40, 100, 1, 0, [7]), (0, 64, 1, 0)]
+    ref = oracle.spectra(X, U, w.dt, w.dirs, grids, wins, [(N, -1.0)], box_L=w.L)
+    Xd, Ud = torch.as_tensor(X, device="cuda"), torch.as_tensor(U, device="cuda")
+
+    def run(inputs, options=None, per_step=False):
+        with R.Radiation(w.dirs, grids, w.dt, [(N, -1.0, 1.0)], wins, box_L=w.L,
+                         options=options) as r:
+            Xi, Ui = inputs
+            if per_step:
+                for s in range(Xi.shape[0]):
+                    r.accumulate(s, Xi[s], Ui[s])
+            else:
+                r.accumulate_steps(0, Xi, Ui)
+            return r.finalize()
+
+    out = {"device": run((Xd, Ud)),
+           "host blocked": run((np.ascontiguousarray(X), np.ascontiguousarray(U))),
+           "graphs": run((Xd, Ud), {"use_graph": 1}, per_step=True),
+           "deferred": run((Xd, Ud), {"defer": 1})}
+    half = N // 2
+    with R.Radiation(w.dirs, grids, w.dt, [(half, -1.0, 1.0)], wins, box_L=w.L) as r:
+        for i in range(2):
+            if i:
+                r.next_shard()
+            sl = slice(i * half, (i + 1) * half)
+            r.accumulate_steps(0, torch.as_tensor(np.ascontiguousarray(X[:, :, sl]), device="cuda"),
+                               torch.as_tensor(np.ascontiguousarray(U[:, :, sl]), device="cuda"))
+        out["two shards"] = r.finalize()
+    for name, got in out.items():
+        assert [g.shape for g in got] == [(3, 64), (1, 64), (8, 64)], name
+        _check(got, ref, 1e-4)
+        for g, e in zip(got, out["device"]):
+            np.testing.assert_allclose(g, e, rtol=1e-9, atol=1e-12 * np.abs(e).max(),
+                                       err_msg=name)
