@@ -46,8 +46,8 @@ METRIC = "G particle·step·ω·n updates/s, FP32 split vs FP64 GPU at ≤1e-4 r
 # workload scaled to 4096 particles (same samples, directions and omegas), valid while
 # the code (comments aside) of the kernel and of its work-list builder is the code that
 # was captured; traffic scales with the particle count.
-TRAFFIC_CAPTURE = {"sources_sha256": "10fc1b54d64fc32862f170357b44e71c81758ebb54752739a8a96edc90ba6d64",
-                   "bytes_per_launch": 696.830464e6, "particles": 4096}
+TRAFFIC_CAPTURE = {"sources_sha256": "81314284c353272c7366b813e661603dfa10d3635b517a38a3470ced5d94372f",
+                   "bytes_per_launch": 697.135104e6, "particles": 4096}
 UNIT = "G updates/s"
 WORKLOAD = 3
 # device memory kept free beside the resident trajectory and one shard's ring
