@@ -130,7 +130,18 @@ typedef struct {
 /* Tuning knobs; zero-initialise for the defaults.  Set before the first step. */
 typedef struct {
     int32_t variant;       /* RAD_VARIANT_*                                  */
-    int32_t anchor_K;      /* FP32 path re-anchor interval: 0 (auto), 8, 16, 32 */
+    int32_t anchor_K;      /* FP32 path re-anchor interval: 8, 16 or 32 samples for
+                              every frequency; 0 with the automatic kernel choice
+                              or a phase budget in reserved[3]: the longest of 8,
+                              16, 32 with w_max (K - 1) dt 2^-24 within the budget
+                              (Sec. 2.2's phase as an FP32 offset), w_max the
+                              highest frequency of all grids; where a lower
+                              frequency tile can take a longer interval and the
+                              kernel build is (or the automatic choice is then
+                              restricted to) 8 SFU frequencies per thread, that
+                              tile takes its own, from its own w_max
+                              (rad_get_options reports the shortest, which
+                              anchors the ring); 0 otherwise: 32              */
     int32_t freq_per_lane; /* 0 (auto), 4, 8 or 16 frequencies per thread      */
     int32_t defer;         /* 1: evaluate every window in one persistent launch at
                               finalize instead of when its last sample arrives */
@@ -152,7 +163,9 @@ typedef struct {
                               first step rad_get_options reports the kernel build
                               in use here (0 for SFU); [2]: host inputs with
                               eager windows: MiB per staging buffer of the
-                              particle-blocked transfer (0: 8192); others must be 0 */
+                              particle-blocked transfer (0: 8192); [3]: FP32 path,
+                              phase budget per update in nanoradians (0: 1e-4 rad),
+                              see anchor_K; others must be 0                       */
 } rad_options;
 
 /*

@@ -117,6 +117,7 @@ struct ChunkMeta {
     int32_t flags;         // kFirstOfTile | kLastOfTile | kFirstOfItem | kLastOfItem
     int32_t real;          // particles of this tile that exist (0..8)
     int32_t grid_len, ftile, row;   // row: the direction's output row in the window
+    int32_t kmul;          // anchor blocks of K << kmul samples
 };
 constexpr int kFirstOfTile = 1, kLastOfTile = 2, kFirstOfItem = 4, kLastOfItem = 8;
 
@@ -132,6 +133,7 @@ struct Smem32 {
     float4 nup[2][32 * FT / 4];                       // the producer's copy for the current item
     float2 anc[2][kComputeWarps][kChunk32 / K];       // phi_ref (hi, lo) per particle, block
     float csh[kComputeWarps][kChunk32 / K];           // centre of each block's offset range
+    float2 cof[kComputeWarps][kChunk32 / K];          // n . (r_a - r_A) per ring anchor block
     float red[kComputeWarps][FT][32];                 // window-close partials
     double run[(COH ? 4 : 1) * FT * 32];              // per-item particle sums (FP64)
     ChunkMeta meta[2];
@@ -191,7 +193,9 @@ struct ChunkCursor {
     }
 };
 
-template <int FT, int NP, int K, bool COH, int MB>
+// BAND: the work items may take anchor blocks of K << kmul samples (a separate
+// build, so that the common build keeps its blocks at the compile-time K).
+template <int FT, int NP, int K, bool COH, int MB, bool BAND = false>
 __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum32Params p)
 {
     static_assert(NP >= 0 && NP < FT, "polynomial frequencies per thread");
@@ -203,6 +207,8 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
     const uint32_t kBytes = (uint32_t)(kChunk32 * cstride * sizeof(float));
     constexpr int kNRun = (COH ? 4 : 1) * FT * 32;
     constexpr int NS = FT - NP;   // SFU frequencies per thread
+    static_assert(K == 8 || K == 16 || K == 32, "ring anchor interval");
+    constexpr int kLog2K = K == 8 ? 3 : (K == 16 ? 4 : 5);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
@@ -267,7 +273,7 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
         float nl0 = 0, nl1 = 0, nl2 = 0, qdt = 0;
         int64_t s0 = 0, s1 = 0, out_off = 0;
         int selb = -1;
-        int grid_len = 0, ftile = 0, row = 0, count = 0, tile0 = 0;
+        int grid_len = 0, ftile = 0, row = 0, count = 0, tile0 = 0, kmul = 0;
         uint32_t L = 0;
         for (; cur.valid; ++L) {
             const int buf = L & 1;
@@ -292,6 +298,7 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                 grid_len = w.grid_len;
                 ftile = it.ftile;
                 row = it.row;
+                kmul = BAND ? it.kmul : 0;
                 tile0 = it.tile0;
 #pragma unroll
                 for (int j = 0; j < FT / 4; ++j) {
@@ -320,10 +327,38 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
             const int64_t cs = c * kChunk32;
             const int lo = (int)((s0 > cs ? s0 : cs) - cs);
             const int hi = (int)((s1 < cs + kChunk32 ? s1 : cs + kChunk32) - cs);
-            // anchor reference phase of (particle pp, block b):
-            //   phi_ref = a dt + h - n . r_a,  a = 32 c + K b   (float-float),
-            // h the centre of the block's offsets (a dt - n . r_a + offset = phi_m):
-            // the offsets (m - a) dt - n . (r_m - r_a) rise monotonically in m
+            // Anchor blocks.  The ring holds anchor positions r_a every K samples;
+            // an item takes its phases in blocks of KE = K << kmul samples (a
+            // longer block for a lower-frequency tile, chosen by the host under
+            // the phase-rounding budget), anchored at the first ring anchor A of
+            // the block.  For kmul > 0 the offsets of the later ring anchors
+            // from A enter the sample offsets as C = n . (r_a - r_A), formed in
+            // float-float from the anchors' hi/lo pairs (the differences are
+            // short, so the hi parts subtract exactly).
+            const int ks = kLog2K + kmul, KE = 1 << ks;
+            if (kmul > 0 && lane < kTileP * NB) {
+                const int pp = lane & (kTileP - 1), b = lane >> 3;
+                const int bA = (b >> kmul) << kmul;
+                float sh = 0.0f, e = 0.0f;
+                const float nh[3] = {n0, n1, n2}, nlo[3] = {nl0, nl1, nl2};
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const ff dh = two_sum(S.tanc[buf][b][q][pp], -S.tanc[buf][bA][q][pp]);
+                    const float dl = dh.lo + (S.tanc[buf][b][3 + q][pp] - S.tanc[buf][bA][3 + q][pp]);
+                    const ff d = two_prod(nh[q], dh.hi);
+                    const float dd = fmaf(nh[q], dl, fmaf(nlo[q], dh.hi, d.lo));
+                    const ff u = two_sum(sh, d.hi);
+                    sh = u.hi;
+                    e = e + (u.lo + dd);
+                }
+                const float chi = sh + e;
+                S.cof[pp][b] = make_float2(chi, e - (chi - sh));
+            }
+            __syncwarp();
+            // anchor reference phase of (particle pp, block B):
+            //   phi_ref = A dt + h - n . r_A,  A = 32 c + KE B   (float-float),
+            // h the centre of the block's offsets (A dt - n . r_A + offset = phi_m):
+            // the offsets (m - A) dt - n . (r_m - r_A) rise monotonically in m
             // (dphi / dt = 1 - n . beta > 0), so h is the mean of the offsets of
             // the block's first and last samples inside the window, and every
             // offset minus h is at most half the block's phase range -- small
@@ -331,24 +366,28 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
             // from samples of the window only, so that the result does not depend
             // on what the ring holds outside it (a block outside the window, or a
             // non-finite offset, takes the range's bound).
-            if (lane < kTileP * NB) {
-                const int pp = lane & (kTileP - 1), b = lane >> 3;
-                const int bl = b * K;
+            if (lane < kTileP * (NB >> kmul)) {
+                const int pp = lane & (kTileP - 1), B = lane >> 3;
+                const int bl = B * KE, bA = B << kmul;
                 const int mlo = lo > bl ? lo : bl;
-                const int mhi = hi - 1 < bl + K - 1 ? hi - 1 : bl + K - 1;
-                float h = 0.5f * (float)(K - 1) * p.dt_hi;
+                const int mhi = hi - 1 < bl + KE - 1 ? hi - 1 : bl + KE - 1;
+                float h = 0.5f * (float)(KE - 1) * p.dt_hi;
                 if (mlo <= mhi) {
                     const float* t0 = &S.tbuf[buf][0][0][0] + mlo * cstride + pp;
                     const float* t1 = &S.tbuf[buf][0][0][0] + mhi * cstride + pp;
-                    const float o0 = (float)(mlo - bl) * p.dt_hi -
-                                     (n0 * t0[0] + n1 * t0[kTileP] + n2 * t0[2 * kTileP]);
-                    const float o1 = (float)(mhi - bl) * p.dt_hi -
-                                     (n0 * t1[0] + n1 * t1[kTileP] + n2 * t1[2 * kTileP]);
+                    float o0 = (float)(mlo - bl) * p.dt_hi -
+                               (n0 * t0[0] + n1 * t0[kTileP] + n2 * t0[2 * kTileP]);
+                    float o1 = (float)(mhi - bl) * p.dt_hi -
+                               (n0 * t1[0] + n1 * t1[kTileP] + n2 * t1[2 * kTileP]);
+                    if (kmul > 0) {
+                        o0 -= S.cof[pp][mlo >> kLog2K].x;
+                        o1 -= S.cof[pp][mhi >> kLog2K].x;
+                    }
                     const float hh = 0.5f * (o0 + o1);
-                    if (fabsf(hh) <= (float)K * p.dt_hi) h = hh;
+                    if (fabsf(hh) <= (float)KE * p.dt_hi) h = hh;
                 }
-                S.csh[pp][b] = h;
-                const float ta = (float)(c * kChunk32 + b * K);
+                S.csh[pp][B] = h;
+                const float ta = (float)(c * kChunk32 + bl);
                 ff t = two_prod(ta, p.dt_hi);
                 float e = fmaf(ta, p.dt_lo, t.lo);
                 const ff th = two_sum(t.hi, h);
@@ -357,7 +396,7 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                 const float nh[3] = {n0, n1, n2}, nlo[3] = {nl0, nl1, nl2};
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    const float rh = S.tanc[buf][b][q][pp], rl = S.tanc[buf][b][3 + q][pp];
+                    const float rh = S.tanc[buf][bA][q][pp], rl = S.tanc[buf][bA][3 + q][pp];
                     const ff d = two_prod(nh[q], rh);
                     const float dl = fmaf(nh[q], rl, fmaf(nlo[q], rh, d.lo));
                     const ff u = two_sum(sh, -d.hi);
@@ -365,7 +404,7 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                     e = e + (u.lo - dl);
                 }
                 const float hi = sh + e;
-                S.anc[buf][pp][b] = make_float2(hi, e - (hi - sh));
+                S.anc[buf][pp][B] = make_float2(hi, e - (hi - sh));
             }
             __syncwarp();
             // geometry: round r handles sample 4 r + lane / 8 of particle lane % 8
@@ -387,13 +426,19 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                 float V1 = -(p1 * dn + q1 * kap) * inv;
                 float V2 = -(p2 * dn + q2 * kap) * inv;
                 if (selb >= 0 && !((__float_as_uint(tb[10 * kTileP]) >> selb) & 1u)) V1 = V2 = 0.0f;
-                // dphi = (sm mod K) dt - h - n . dr, compensated
-                const float ti = (float)(sm & (K - 1));
+                // dphi = (sm mod KE) dt - h - n . dr (- C), compensated
+                const float ti = (float)(sm & (KE - 1));
                 const ff t = two_prod(ti, p.dt_hi);
                 float e = fmaf(ti, p.dt_lo, t.lo);
-                const ff th = two_sum(t.hi, -S.csh[pp][sm / K]);
+                const ff th = two_sum(t.hi, -S.csh[pp][sm >> ks]);
                 float sh = th.hi;
                 e = e + th.lo;
+                if (kmul > 0) {
+                    const float2 cf = S.cof[pp][sm >> kLog2K];
+                    const ff u = two_sum(sh, -cf.x);
+                    sh = u.hi;
+                    e = e + (u.lo - cf.y);
+                }
                 const float dr[3] = {tb[0], tb[kTileP], tb[2 * kTileP]};
                 const float nh[3] = {n0, n1, n2}, nlo[3] = {nl0, nl1, nl2};
 #pragma unroll
@@ -429,6 +474,7 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                 M.grid_len = grid_len;
                 M.ftile = ftile;
                 M.row = row;
+                M.kmul = kmul;
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&S.gfull[buf]);
@@ -464,6 +510,7 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
         if (ii < 0 || *abort_flag) break;
         const int flags = S.meta[buf].flags;
         const int lo = S.meta[buf].lo, hi = S.meta[buf].hi;
+        const int ks = kLog2K + (BAND ? S.meta[buf].kmul : 0);   // blocks of 1 << ks samples
         if (flags & kFirstOfItem) {
             const WorkItem it = p.items[ii];
             const WinDev w = p.wins[it.win];
@@ -481,9 +528,9 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
         // update loop, one anchor block at a time; the next sample's geometry
         // is loaded while the current one is accumulated
 #pragma unroll 1
-        for (int b = lo / K; b * K < hi; ++b) {
-            const int l0 = lo > b * K ? lo : b * K;
-            const int l1 = hi < b * K + K ? hi : b * K + K;
+        for (int b = lo >> ks; (b << ks) < hi; ++b) {
+            const int l0 = lo > (b << ks) ? lo : (b << ks);
+            const int l1 = hi < ((b + 1) << ks) ? hi : ((b + 1) << ks);
             // anchor phases Theta_k = 2 pi frac(nu_k phi_ref): float-float
             // product, exact reduction to one turn; halved for the polynomial
             // frequencies
@@ -600,10 +647,10 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
     }
 }
 
-template <int FT, int NP, int K, bool COH, int MB>
+template <int FT, int NP, int K, bool COH, int MB, bool BAND = false>
 cudaError_t launch32_one(const Accum32Params& p, int grid, cudaStream_t st)
 {
-    auto kern = accum32_kernel<FT, NP, K, COH, MB>;
+    auto kern = accum32_kernel<FT, NP, K, COH, MB, BAND>;
     const size_t smem = smem32_bytes<FT, NP, K, COH>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -612,14 +659,14 @@ cudaError_t launch32_one(const Accum32Params& p, int grid, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template <int FT, int NP, int K, bool COH, int MB>
+template <int FT, int NP, int K, bool COH, int MB, bool BAND = false>
 int blocks32_one()
 {
     int nb = 0;
     const size_t smem = smem32_bytes<FT, NP, K, COH>();
-    if (cudaFuncSetAttribute(accum32_kernel<FT, NP, K, COH, MB>,
+    if (cudaFuncSetAttribute(accum32_kernel<FT, NP, K, COH, MB, BAND>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, accum32_kernel<FT, NP, K, COH, MB>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, accum32_kernel<FT, NP, K, COH, MB, BAND>,
                                                       kBlockThreads, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;

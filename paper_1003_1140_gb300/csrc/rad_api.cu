@@ -107,6 +107,8 @@ struct rad_ctx {
     rad_options opt{};
     Accum32Config cfg{8, 0, 16, false, 2};
     int K = 16;                    // anchor interval used by the ingest
+    bool per_band_K = false;       // FP32 path: each frequency tile's anchor blocks are the
+                                   // longest multiple K << m within the phase budget
     int nsub = 1;                  // sub-samples per PIC sample
     bool frozen = false;           // options frozen after the first step
 
@@ -270,6 +272,7 @@ static void basis(const double n[3], double e1[3], double e2[3])
 bool rad::accum32_dispatch(const Accum32Params* p, const Accum32Config& cfg, int grid,
                            cudaStream_t st, cudaError_t* err, int* nb)
 {
+    if (cfg.band) return accum32_band(p, cfg, grid, st, err, nb);
     return accum32_ft8_sfu(p, cfg, grid, st, err, nb) || accum32_ft8_mix(p, cfg, grid, st, err, nb) ||
            accum32_ft16(p, cfg, grid, st, err, nb) || accum32_ft4(p, cfg, grid, st, err, nb);
 }
@@ -280,6 +283,8 @@ static int freq_tile(const rad_ctx* c)
 {
     return c->precision == RAD_FP64 ? 32 * accum64_ft() : 32 * c->cfg.ft;
 }
+
+static std::vector<std::vector<int>> band_kmul(const rad_ctx* c, int ftl);
 
 // Build the work items of one event (set of windows) and sort them by cost;
 // with `ranges` only the particle tiles [first, second) of each species (the
@@ -309,6 +314,7 @@ static void build_items(rad_ctx* c, Event& ev, int total_blocks,
     // work); an item costs one list fetch and one FP64 flush of its sums
     const double target_items = 256.0 * std::max(1, total_blocks);
     int G = (int)std::max(1.0, std::floor(units / target_items));
+    const std::vector<std::vector<int>> km = band_kmul(c, ftl);
     ev.items.clear();
     std::vector<int64_t> cost;
     for (int w : ev.wins) {
@@ -327,7 +333,8 @@ static void build_items(rad_ctx* c, Event& ev, int total_blocks,
             for (int t0 = std::max(0, lo_of(s)); t0 < t_end; t0 += G)
                 for (int row = 0; row < (int)wd.size(); ++row)
                     for (int f = 0; f < nft; ++f) {
-                        WorkItem it{w, wd[row], f, s, t0, std::min(G, t_end - t0), row, 0};
+                        WorkItem it{w, wd[row], f, s, t0, std::min(G, t_end - t0), row,
+                                    km[W.freq_grid][f]};
                         ev.items.push_back(it);
                         cost.push_back((int64_t)it.ntiles * nch);
                     }
@@ -369,22 +376,56 @@ static cudaEvent_t next_event(std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& 
 // autotuner for the FP32 kernel variant (variant = RAD_VARIANT_AUTO)
 // ---------------------------------------------------------------------------
 // Largest anchor interval K whose worst-case rounding of the offset phase per
-// update, w_max * |dphi|_max * 2^-24, stays within 1e-4 rad; the offsets are
-// centred in their block, so |dphi| <= (K - 1) dt (1 - n.beta) / 2 <= (K - 1) dt.
-// (The special-function unit's own reduction of the radian argument adds about
-// 1.3e-7 |theta| rad, and the FP32 roundings of w and dphi add errors of the
-// same order, all proportional to |dphi|.)
+// update, w_max * |dphi|_max * 2^-24, stays within the phase budget (1e-4 rad
+// unless the options give one); the offsets are centred in their block, so
+// |dphi| <= (K - 1) dt (1 - n.beta) / 2 <= (K - 1) dt.  (The special-function
+// unit's own reduction of the radian argument adds about 1.3e-7 |theta| rad,
+// and the FP32 roundings of w and dphi add errors of the same order, all
+// proportional to |dphi|.)
+static double phase_budget(const rad_ctx* c)
+{
+    return c->opt.reserved[3] > 0 ? c->opt.reserved[3] * 1e-9 : 1e-4;
+}
+
+static int budget_K_at(const rad_ctx* c, double wmax)
+{
+    for (int K : {32, 16}) {
+        const double err = wmax * (K - 1) * (c->dt / c->nsub) * std::ldexp(1.0, -24);
+        if (err <= phase_budget(c)) return K;
+    }
+    return 8;
+}
+
 static int budget_K(const rad_ctx* c)
 {
     double wmax = 0.0;
     for (int g = 0; g < c->n_grids; ++g)
         for (int k = 0; k < c->grid_len[g]; ++k)
             wmax = std::max(wmax, std::fabs(c->h_freqs[c->grid_off[g] + k]));
-    for (int K : {32, 16}) {
-        const double err = wmax * (K - 1) * (c->dt / c->nsub) * std::ldexp(1.0, -24);
-        if (err <= 1e-4) return K;
+    return budget_K_at(c, wmax);
+}
+
+// Per frequency tile of each grid, the anchor blocks' multiple of the ring's K
+// (as a shift): the longest interval K << m, up to one chunk, within the phase
+// budget at the tile's highest frequency.  The ring is anchored at the K of the
+// highest frequency of all grids, so a lower band takes fewer, longer blocks.
+// All zero unless the context chose its K by the budget.
+static std::vector<std::vector<int>> band_kmul(const rad_ctx* c, int ftl)
+{
+    std::vector<std::vector<int>> km(c->n_grids);
+    for (int g = 0; g < c->n_grids; ++g) {
+        const int nft = (c->grid_len[g] + ftl - 1) / ftl;
+        km[g].assign(nft, 0);
+        if (!c->per_band_K) continue;
+        for (int f = 0; f < nft; ++f) {
+            double wmax = 0.0;
+            for (int k = f * ftl; k < std::min((f + 1) * ftl, c->grid_len[g]); ++k)
+                wmax = std::max(wmax, std::fabs(c->h_freqs[c->grid_off[g] + k]));
+            const int Kt = std::min(budget_K_at(c, wmax), kChunk32);
+            while ((c->K << (km[g][f] + 1)) <= Kt) ++km[g][f];
+        }
     }
-    return 8;
+    return km;
 }
 
 static std::string tune_cache_path()
@@ -409,7 +450,7 @@ static std::string tune_key(const rad_ctx* c, int K)
         k << (W.s1 - W.s0) << ":" << W.species_mask << ":" << W.freq_grid << ":"
           << c->win_dirs[w].size() << ",";
     }
-    k << "|d" << c->opt.defer << "|n" << std::max(1, c->opt.subcycle);
+    k << "|d" << c->opt.defer << "|n" << std::max(1, c->opt.subcycle) << "|b" << c->cfg.band;
     return k.str();
 }
 
@@ -472,6 +513,7 @@ static void tune_slice(const rad_ctx* c, Event& ev, size_t n)
     const rad_window& W = c->wins[best];
     const int ftl = freq_tile(c);
     const int nft = (c->grid_len[W.freq_grid] + ftl - 1) / ftl;
+    const std::vector<std::vector<int>> km = band_kmul(c, ftl);
     const std::vector<int32_t>& wd = c->win_dirs[best];
     for (int s = 0; s < c->n_species && ev.items.size() < n; ++s) {
         if (!((W.species_mask >> s) & 1u)) continue;
@@ -479,7 +521,7 @@ static void tune_slice(const rad_ctx* c, Event& ev, size_t n)
         for (int t = 0; t < nt && ev.items.size() < n; ++t)
             for (int row = 0; row < (int)wd.size() && ev.items.size() < n; ++row)
                 for (int f = 0; f < nft && ev.items.size() < n; ++f)
-                    ev.items.push_back(WorkItem{best, wd[row], f, s, t, 1, row, 0});
+                    ev.items.push_back(WorkItem{best, wd[row], f, s, t, 1, row, km[W.freq_grid][f]});
     }
 }
 
@@ -498,6 +540,7 @@ static int autotune32(rad_ctx* c, int K)
     const bool coh = c->mode == RAD_COHERENT;
     std::vector<Accum32Config> cands = {{8, 0, K, coh, 2}, {8, 0, K, coh, 3}, {8, 1, K, coh, 2},
                                         {8, 1, K, coh, 3}, {8, 2, K, coh, 2}, {4, 0, K, coh, 4}};
+    if (c->cfg.band) cands = {{8, 0, K, coh, 2, true}, {8, 0, K, coh, 3, true}};
     // small problems: not worth timing
     if (rad_updates(c) < (int64_t)2e10) {
         c->cfg = cands[0];
@@ -618,9 +661,24 @@ static int freeze(rad_ctx* c)
             return fail(c, RAD_EINVAL, "8 frequencies per thread is built for 2 or 3 blocks per SM");
         const bool tune = c->opt.variant == RAD_VARIANT_AUTO && !c->opt.freq_per_lane &&
                           !c->opt.blocks_per_sm;
-        if (!c->opt.anchor_K && tune) {
+        c->per_band_K = false;
+        if (!c->opt.anchor_K && (tune || c->opt.reserved[3] > 0)) {
             c->K = budget_K(c);
             c->cfg.K = c->K;
+            // longer anchor blocks for the lower bands where any frequency tile
+            // can take one: the 8-SFU-frequency build with per-item blocks
+            if (tune || (c->cfg.ft == 8 && c->cfg.np == 0)) {
+                c->per_band_K = true;
+                bool any = false;
+                for (const auto& g : band_kmul(c, 32 * 8))
+                    for (int m : g) any = any || m > 0;
+                c->per_band_K = any;
+            }
+        }
+        c->cfg.band = c->per_band_K;
+        if (c->per_band_K) {
+            c->cfg.ft = 8;
+            c->cfg.np = 0;
         }
         // anchor positions: one FP32 hi/lo 3-vector per particle per K samples of the ring
         c->nblk = c->ring / c->K;
@@ -1367,6 +1425,7 @@ int rad_set_options(rad_ctx* c, const rad_options* o)
     if (o->freq_per_lane != 0 && o->freq_per_lane != 4 && o->freq_per_lane != 8 &&
         o->freq_per_lane != 16)
         return fail(c, RAD_EINVAL, "freq_per_lane must be 0, 4, 8 or 16");
+    if (o->reserved[3] < 0) return fail(c, RAD_EINVAL, "phase budget must be >= 0");
     if (o->subcycle < 0 || o->subcycle > 64)
         return fail(c, RAD_EINVAL, "subcycle must be in [0, 64]");
     if (o->blocks_per_sm != 0 && o->blocks_per_sm != 2 && o->blocks_per_sm != 3 &&

@@ -52,7 +52,7 @@ struct WorkItem {
     int32_t tile0;    // first particle tile (column / 8)
     int32_t ntiles;   // number of particle tiles
     int32_t row;      // output row of the direction in the window's [dirs][len] block
-    int32_t pad_;
+    int32_t kmul;     // FP32 path: phases anchored every K << kmul samples (K: the ring's)
 };
 
 // Per-window constants the accumulation kernels read.
@@ -314,9 +314,12 @@ struct Accum32Config {
     int ft, np, K;
     bool coh;
     int mb;
+    bool band = false;   // items with anchor blocks of K << kmul (8 SFU frequencies per thread)
 };
 bool accum32_ft8_sfu(const Accum32Params* p, const Accum32Config& cfg, int grid,
                      cudaStream_t st, cudaError_t* err, int* nb);
+bool accum32_band(const Accum32Params* p, const Accum32Config& cfg, int grid,
+                  cudaStream_t st, cudaError_t* err, int* nb);
 bool accum32_ft8_mix(const Accum32Params* p, const Accum32Config& cfg, int grid,
                      cudaStream_t st, cudaError_t* err, int* nb);
 bool accum32_ft16(const Accum32Params* p, const Accum32Config& cfg, int grid,

@@ -252,6 +252,9 @@ class Radiation:
                 o.reserved[1] = int(v)
             elif k == "host_stage_mib":
                 o.reserved[2] = int(v)
+            elif k == "phase_budget":
+                # radians per update, passed as whole nanoradians
+                o.reserved[3] = int(round(float(v) * 1e9))
             else:
                 setattr(o, k, int(v))
         self._check(self._lib.rad_set_options(self._h, ctypes.byref(o)))
@@ -281,6 +284,7 @@ class Radiation:
         self._check(self._lib.rad_get_options(self._h, ctypes.byref(o)))
         out = {f: getattr(o, f) for f, _ in rad_options._fields_ if f != "reserved"}
         out["poly_per_lane"] = int(o.reserved[1])
+        out["phase_budget"] = o.reserved[3] * 1e-9
         return out
 
     def accumulate(self, step, x, u):
