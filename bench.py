@@ -576,6 +576,19 @@ def main():
             "upper_decade_worst_bin_vs_fp64": float((np.abs(Sb - S64) / S64)[:, hi].max()),
             "rel_l2_max": float((np.linalg.norm(Sb - S64, axis=1) / np.linalg.norm(S64, axis=1)).max()),
             "kernel_rate": upd64 / (tb["accum_ms"] * 1e-3) / 1e9}
+        # and with the precise phase (float-float offsets, reduced to one turn)
+        cp = R.Radiation(w.dirs, w.grids, w.dt, [(n64, q, mass)], w.windows,
+                         precision=R.RAD_FP32_SPLIT, box_L=w.L,
+                         options={"variant": R.RAD_VARIANT_PRECISE})
+        cp.accumulate_steps(0, X64, U64)
+        Sp = cp.finalize()[0]
+        tp = cp.timing()
+        cp.close()
+        perbin["precise_phase"] = {
+            "upper_decade_worst_bin_vs_fp64": float((np.abs(Sp - S64) / S64)[:, hi].max()),
+            "worst_bin_vs_fp64": float((np.abs(Sp - S64) / S64).max()),
+            "rel_l2_max": float((np.linalg.norm(Sp - S64, axis=1) / np.linalg.norm(S64, axis=1)).max()),
+            "kernel_rate": upd64 / (tp["accum_ms"] * 1e-3) / 1e9}
         fp64_rate = upd64 / (t64["accum_ms"] * 1e-3) / 1e9
         fp64 = {"value": fp64_rate, "unit": UNIT,
                 "sample": f"first {n64} particles, same samples/dirs/omegas"}

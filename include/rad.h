@@ -83,6 +83,10 @@ extern "C" {
 #define RAD_VARIANT_AUTO 0   /* autotuned (or the cached choice) */
 #define RAD_VARIANT_SFU 1    /* every e^{i theta} by the special-function unit */
 #define RAD_VARIANT_MIX 2    /* some frequencies by an FMA-pipe polynomial (see reserved[1]) */
+#define RAD_VARIANT_PRECISE 3 /* the offset phase nu dphi in float-float, reduced to one
+                                 turn before the special-function unit: per-update phase
+                                 error ~5e-7 rad instead of ~1e-7 |omega dphi|; 8
+                                 frequencies per thread, anchor interval 32          */
 
 typedef struct rad_ctx rad_ctx;
 

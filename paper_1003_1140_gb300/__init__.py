@@ -6,9 +6,9 @@ close and the finalize -- runs in ``_build/librad.so`` built from ``csrc/``.
 ``rad`` is a ctypes binding with the same entry points as ``include/rad.h``.
 """
 from .rad import (RAD_COHERENT, RAD_FP32_SPLIT, RAD_FP64, RAD_INCOHERENT, RAD_VARIANT_AUTO,
-                  RAD_VARIANT_MIX, RAD_VARIANT_SFU, RadError, Radiation, load,
+                  RAD_VARIANT_MIX, RAD_VARIANT_PRECISE, RAD_VARIANT_SFU, RadError, Radiation, load,
                   spectrum_from_sums)
 
 __all__ = ["Radiation", "RadError", "load", "RAD_COHERENT", "RAD_INCOHERENT", "RAD_FP32_SPLIT",
            "RAD_FP64", "RAD_VARIANT_AUTO", "RAD_VARIANT_SFU", "RAD_VARIANT_MIX",
-           "spectrum_from_sums"]
+           "RAD_VARIANT_PRECISE", "spectrum_from_sums"]

@@ -91,12 +91,14 @@ __device__ __forceinline__ void poly_cis_half(float h, float& c2, float& s2half)
 // pass brings a large-|x| remainder into [-1/2, 1/2].
 __device__ __forceinline__ float anchor_turns(float nh, float nl, float2 an)
 {
-    const float pr = nh * an.x;
+    // __fmul_rn / __fadd_rn: the rounded product pr must not be re-formed as a
+    // fused multiply-add inside the sums below (pe holds its rounding error)
+    const float pr = __fmul_rn(nh, an.x);
     const float pe = fmaf(nh, an.x, -pr);
     const float tl = fmaf(nl, an.x, fmaf(nh, an.y, pe));
-    float fr = pr - ((pr + kMagic) - kMagic);
-    fr = fr - ((fr + kMagic) - kMagic);
-    return fr + tl;
+    float fr = __fsub_rn(pr, __fsub_rn(__fadd_rn(pr, kMagic), kMagic));
+    fr = __fsub_rn(fr, __fsub_rn(__fadd_rn(fr, kMagic), kMagic));
+    return __fadd_rn(fr, tl);
 }
 
 // Shared-memory slot of lane l's j-th float4 of frequencies: l * FT/4 + j, with j
@@ -121,10 +123,10 @@ struct ChunkMeta {
 };
 constexpr int kFirstOfTile = 1, kLastOfTile = 2, kFirstOfItem = 4, kLastOfItem = 8;
 
-template <int FT, int K, bool COH>
+template <int FT, int K, bool COH, bool PREC = false>
 struct Smem32 {
-    float tbuf[2][kChunk32][kComps][kTileP];          // bulk-copy destinations (producer only;
-                                                      // a chunk fills comps of the kComps rows)
+    float tbuf[2][kChunk32][PREC ? kCompsPrec : kComps][kTileP];   // bulk-copy destinations
+                                                      // (producer only; a chunk fills comps rows)
     float tanc[2][kChunk32 / K][6][kTileP];           // the chunk's anchor positions (hi, lo)
     float4 geo[2][kComputeWarps][kChunk32 + 1];       // V1, V2, dphi per particle and sample
     // the item's nu = w / 2 pi as float-float (hi, lo): lane l's FT values as
@@ -155,10 +157,10 @@ __device__ __forceinline__ void compute_sync(uint64_t* bar, uint32_t& phase, int
     ++phase;
 }
 
-template <int FT, int NP, int K, bool COH>
+template <int FT, int NP, int K, bool COH, bool PREC = false>
 constexpr size_t smem32_bytes()
 {
-    return sizeof(Smem32<FT, K, COH>) + 128;
+    return sizeof(Smem32<FT, K, COH, PREC>) + 128;
 }
 
 // The producer's walk over (item, tile, chunk): items come from an atomic
@@ -195,12 +197,14 @@ struct ChunkCursor {
 
 // BAND: the work items may take anchor blocks of K << kmul samples (a separate
 // build, so that the common build keeps its blocks at the compile-time K).
-template <int FT, int NP, int K, bool COH, int MB, bool BAND = false>
+// PREC: the offset phase nu * dphi in float-float, reduced to one turn before
+// the special-function unit (the precise-phase variant).
+template <int FT, int NP, int K, bool COH, int MB, bool BAND = false, bool PREC = false>
 __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum32Params p)
 {
     static_assert(NP >= 0 && NP < FT, "polynomial frequencies per thread");
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    auto& S = *reinterpret_cast<Smem32<FT, K, COH>*>(
+    auto& S = *reinterpret_cast<Smem32<FT, K, COH, PREC>*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     // one chunk of the ring: 32 samples x comps components x 8 particles
     const int cstride = p.comps * kTileP;
@@ -444,12 +448,14 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     const ff d = two_prod(nh[q], dr[q]);
-                    const float dl = fmaf(nlo[q], dr[q], d.lo);
+                    float dl = fmaf(nlo[q], dr[q], d.lo);
+                    if (PREC) dl = fmaf(nh[q], tb[(11 + q) * kTileP], dl);   // n . dr_lo
                     const ff u = two_sum(sh, -d.hi);
                     sh = u.hi;
                     e = e + (u.lo - dl);
                 }
-                S.geo[buf][pp][sm] = make_float4(V1, V2, sh + e, 0.0f);
+                const float dh = sh + e;
+                S.geo[buf][pp][sm] = make_float4(V1, V2, dh, PREC ? e - (dh - sh) : 0.0f);
             }
             __syncwarp();
             // the item's frequencies (nu hi, lo) for the compute warps, which turn
@@ -498,10 +504,11 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
     }
 
     // ---------------------------------------------------------------- compute
-    float om[FT];   // omega (SFU) or omega / 2 (polynomial)
+    float om[FT];   // omega (SFU), omega / 2 (polynomial) or nu_hi = omega / 2 pi (PREC)
+    float nlo[FT];  // PREC: nu_lo
     float a1r[FT], a1i[FT], a2r[FT], a2i[FT], th[FT];
 #pragma unroll
-    for (int i = 0; i < FT; ++i) om[i] = a1r[i] = a1i[i] = a2r[i] = a2i[i] = th[i] = 0.0f;
+    for (int i = 0; i < FT; ++i) om[i] = nlo[i] = a1r[i] = a1i[i] = a2r[i] = a2i[i] = th[i] = 0.0f;
     uint32_t cphase = 0;
     for (uint32_t L = 0;; ++L) {
         const int buf = L & 1;
@@ -517,8 +524,13 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
 #pragma unroll
             for (int i = 0; i < FT; ++i) {
                 const int k = it.ftile * (32 * FT) + lane + 32 * i;
-                const float wk = (k < w.grid_len) ? p.omega[w.grid_off + k] : 0.0f;
-                om[i] = (i < NS) ? wk : 0.5f * wk;
+                if (PREC) {
+                    om[i] = (k < w.grid_len) ? p.nu_hi[w.grid_off + k] : 0.0f;
+                    nlo[i] = (k < w.grid_len) ? p.nu_lo[w.grid_off + k] : 0.0f;
+                } else {
+                    const float wk = (k < w.grid_len) ? p.omega[w.grid_off + k] : 0.0f;
+                    om[i] = (i < NS) ? wk : 0.5f * wk;
+                }
             }
         }
         if (flags & kFirstOfTile) {
@@ -543,8 +555,9 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int i = 4 * j + q;
-                    th[i] = anchor_turns(nh[q], nl[q], an) *
-                            (i < NS ? 6.28318530717958647f : 3.14159265358979323f);
+                    th[i] = PREC ? anchor_turns(nh[q], nl[q], an)
+                                 : anchor_turns(nh[q], nl[q], an) *
+                                       (i < NS ? 6.28318530717958647f : 3.14159265358979323f);
                 }
             }
             float4 gg = S.geo[buf][warp][l0];
@@ -553,7 +566,20 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                 const float4 gn = S.geo[buf][warp][(l + 1) & (kChunk32 - 1)];
 #pragma unroll
                 for (int i = 0; i < NS; ++i) {
-                    const float tt = fmaf(om[i], gg.z, th[i]);
+                    float tt;
+                    if (PREC) {
+                        // turns: nu dphi = p + (p's rounding error) + nu_lo dphi_hi
+                        // + nu_hi dphi_lo (+ Theta); p's integer part removed exactly
+                        const float pr = __fmul_rn(om[i], gg.z);
+                        float c = fmaf(om[i], gg.z, -pr);
+                        c = fmaf(nlo[i], gg.z, c);
+                        c = fmaf(om[i], gg.w, c);
+                        c = __fadd_rn(c, th[i]);
+                        const float r = __fsub_rn(__fadd_rn(pr, kMagic), kMagic);
+                        tt = __fmul_rn(__fadd_rn(__fsub_rn(pr, r), c), 6.28318530717958647f);
+                    } else {
+                        tt = fmaf(om[i], gg.z, th[i]);
+                    }
                     float sn, cs_;
                     __sincosf(tt, &sn, &cs_);
                     a1r[i] = fmaf(gg.x, cs_, a1r[i]);
@@ -647,11 +673,11 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
     }
 }
 
-template <int FT, int NP, int K, bool COH, int MB, bool BAND = false>
+template <int FT, int NP, int K, bool COH, int MB, bool BAND = false, bool PREC = false>
 cudaError_t launch32_one(const Accum32Params& p, int grid, cudaStream_t st)
 {
-    auto kern = accum32_kernel<FT, NP, K, COH, MB, BAND>;
-    const size_t smem = smem32_bytes<FT, NP, K, COH>();
+    auto kern = accum32_kernel<FT, NP, K, COH, MB, BAND, PREC>;
+    const size_t smem = smem32_bytes<FT, NP, K, COH, PREC>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -659,14 +685,14 @@ cudaError_t launch32_one(const Accum32Params& p, int grid, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template <int FT, int NP, int K, bool COH, int MB, bool BAND = false>
+template <int FT, int NP, int K, bool COH, int MB, bool BAND = false, bool PREC = false>
 int blocks32_one()
 {
     int nb = 0;
-    const size_t smem = smem32_bytes<FT, NP, K, COH>();
-    if (cudaFuncSetAttribute(accum32_kernel<FT, NP, K, COH, MB, BAND>,
+    const size_t smem = smem32_bytes<FT, NP, K, COH, PREC>();
+    if (cudaFuncSetAttribute(accum32_kernel<FT, NP, K, COH, MB, BAND, PREC>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, accum32_kernel<FT, NP, K, COH, MB, BAND>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, accum32_kernel<FT, NP, K, COH, MB, BAND, PREC>,
                                                       kBlockThreads, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;

@@ -120,7 +120,8 @@ struct rad_ctx {
 
     // ring
     int64_t ring = 0, nblk = 0;
-    int comps = kCompsPlain;       // + the selector-flags word once selectors are defined
+    int comps = kCompsPlain;       // + the selector-flags word once selectors are defined;
+                                   // kCompsPrec for the precise-phase variant
     float* slab32 = nullptr;
     double* slab64 = nullptr;
     float* anc32 = nullptr;
@@ -272,6 +273,7 @@ static void basis(const double n[3], double e1[3], double e2[3])
 bool rad::accum32_dispatch(const Accum32Params* p, const Accum32Config& cfg, int grid,
                            cudaStream_t st, cudaError_t* err, int* nb)
 {
+    if (cfg.prec) return accum32_precise(p, cfg, grid, st, err, nb);
     if (cfg.band) return accum32_band(p, cfg, grid, st, err, nb);
     return accum32_ft8_sfu(p, cfg, grid, st, err, nb) || accum32_ft8_mix(p, cfg, grid, st, err, nb) ||
            accum32_ft16(p, cfg, grid, st, err, nb) || accum32_ft4(p, cfg, grid, st, err, nb);
@@ -450,7 +452,8 @@ static std::string tune_key(const rad_ctx* c, int K)
         k << (W.s1 - W.s0) << ":" << W.species_mask << ":" << W.freq_grid << ":"
           << c->win_dirs[w].size() << ",";
     }
-    k << "|d" << c->opt.defer << "|n" << std::max(1, c->opt.subcycle) << "|b" << c->cfg.band;
+    k << "|d" << c->opt.defer << "|n" << std::max(1, c->opt.subcycle) << "|b" << c->cfg.band
+      << "|p" << c->cfg.prec;
     return k.str();
 }
 
@@ -541,6 +544,7 @@ static int autotune32(rad_ctx* c, int K)
     std::vector<Accum32Config> cands = {{8, 0, K, coh, 2}, {8, 0, K, coh, 3}, {8, 1, K, coh, 2},
                                         {8, 1, K, coh, 3}, {8, 2, K, coh, 2}, {4, 0, K, coh, 4}};
     if (c->cfg.band) cands = {{8, 0, K, coh, 2, true}, {8, 0, K, coh, 3, true}};
+    if (c->cfg.prec) cands = {{8, 0, K, coh, 2, false, true}, {8, 0, K, coh, 3, false, true}};
     // small problems: not worth timing
     if (rad_updates(c) < (int64_t)2e10) {
         c->cfg = cands[0];
@@ -620,6 +624,16 @@ static int freeze(rad_ctx* c)
 {
     if (c->frozen) return RAD_OK;
     CU(cudaSetDevice(c->device));
+    if (c->precision == RAD_FP32_SPLIT && c->opt.variant == RAD_VARIANT_PRECISE &&
+        c->comps != kCompsPrec) {
+        // the precise-phase ring also carries the lo part of each position offset
+        CU(cudaFree(c->slab32));
+        c->slab32 = nullptr;
+        c->comps = kCompsPrec;
+        const size_t bytes = (size_t)c->ring * c->comps * c->ncols * sizeof(float);
+        CU(cudaMalloc(&c->slab32, bytes));
+        CU(cudaMemset(c->slab32, 0, bytes));
+    }
     if (c->opt.subcycle > 1 && c->nsub == 1) {
         // sub-cycling: the ring holds nsub samples per PIC sample, windows and
         // the per-sample weight dt are in sub-sample units
@@ -659,10 +673,18 @@ static int freeze(rad_ctx* c)
             return fail(c, RAD_EINVAL, "4 frequencies per thread is built for 4 blocks per SM, SFU only");
         if (c->cfg.ft == 8 && c->cfg.mb == 4)
             return fail(c, RAD_EINVAL, "8 frequencies per thread is built for 2 or 3 blocks per SM");
-        const bool tune = c->opt.variant == RAD_VARIANT_AUTO && !c->opt.freq_per_lane &&
+        const bool prec = c->opt.variant == RAD_VARIANT_PRECISE;
+        c->cfg.prec = prec;
+        if (prec) {
+            // one turn of phase per update regardless of K: the ring's anchor
+            // interval stays at 32
+            c->K = 32;
+            c->cfg.K = 32;
+        }
+        const bool tune = (c->opt.variant == RAD_VARIANT_AUTO || prec) && !c->opt.freq_per_lane &&
                           !c->opt.blocks_per_sm;
         c->per_band_K = false;
-        if (!c->opt.anchor_K && (tune || c->opt.reserved[3] > 0)) {
+        if (!prec && !c->opt.anchor_K && (tune || c->opt.reserved[3] > 0)) {
             c->K = budget_K(c);
             c->cfg.K = c->K;
             // longer anchor blocks for the lower bands where any frequency tile
@@ -1419,7 +1441,13 @@ int rad_set_options(rad_ctx* c, const rad_options* o)
 {
     if (!c || !o) return RAD_EINVAL;
     if (c->frozen) return fail(c, RAD_ESTATE, "options must be set before the first step");
-    if (o->variant < 0 || o->variant > 2) return fail(c, RAD_EINVAL, "variant out of range");
+    if (o->variant < 0 || o->variant > 3) return fail(c, RAD_EINVAL, "variant out of range");
+    if (o->variant == RAD_VARIANT_PRECISE &&
+        ((o->anchor_K != 0 && o->anchor_K != 32) || (o->freq_per_lane != 0 && o->freq_per_lane != 8) ||
+         o->blocks_per_sm == 4))
+        return fail(c, RAD_EINVAL,
+                    "the precise-phase variant is built for anchor_K 32, 8 frequencies per thread, "
+                    "2 or 3 blocks per SM");
     if (o->anchor_K != 0 && o->anchor_K != 8 && o->anchor_K != 16 && o->anchor_K != 32)
         return fail(c, RAD_EINVAL, "anchor_K must be 0, 8, 16 or 32");
     if (o->freq_per_lane != 0 && o->freq_per_lane != 4 && o->freq_per_lane != 8 &&
@@ -1507,7 +1535,8 @@ int rad_get_options(const rad_ctx* c, rad_options* o)
         o->anchor_K = c->cfg.K;
         o->freq_per_lane = c->cfg.ft;
         o->blocks_per_sm = c->cfg.mb;
-        o->variant = c->cfg.np > 0 ? RAD_VARIANT_MIX : RAD_VARIANT_SFU;
+        o->variant = c->cfg.prec ? RAD_VARIANT_PRECISE
+                                 : (c->cfg.np > 0 ? RAD_VARIANT_MIX : RAD_VARIANT_SFU);
         o->reserved[1] = c->cfg.np;
     }
     return RAD_OK;

@@ -261,7 +261,10 @@ __global__ void __launch_bounds__(64, 8) ingest_kernel(const IngestParams p)
                     }
                     float* o = p.slab32 + (tile * p.ring + sl) * (p.comps * kTileP) + pp;
                     for (int c = 0; c < 3; ++c) {
-                        o[c * kTileP] = (float)(rk[c] - ra[c]);
+                        const double d = rk[c] - ra[c];
+                        const float dh = (float)d;
+                        o[c * kTileP] = dh;
+                        if (p.comps >= kCompsPrec) o[(11 + c) * kTileP] = (float)(d - (double)dh);
                         o[(3 + c) * kTileP] = (float)bk[c];
                         o[(6 + c) * kTileP] = (float)bd[c];
                     }
@@ -318,9 +321,13 @@ __global__ void __launch_bounds__(64, 8) ingest_kernel(const IngestParams p)
             const float corr = dus / (gq * gm * (gq + gm));
             const float idt = (float)(1.0 / p.dt);
             float* o = p.slab32 + (tile * p.ring + slot) * (p.comps * kTileP) + pp;
-            o[0 * kTileP] = (float)(rp[0] - ra[0]);
-            o[1 * kTileP] = (float)(rp[1] - ra[1]);
-            o[2 * kTileP] = (float)(rp[2] - ra[2]);
+            for (int c = 0; c < 3; ++c) {
+                const double d = rp[c] - ra[c];
+                const float dh = (float)d;
+                o[c * kTileP] = dh;
+                // precise-phase ring: the rounding of the offset as its lo part
+                if (p.comps >= kCompsPrec) o[(11 + c) * kTileP] = (float)(d - (double)dh);
+            }
             o[3 * kTileP] = ub[0] * igb;
             o[4 * kTileP] = ub[1] * igb;
             o[5 * kTileP] = ub[2] * igb;

@@ -16,7 +16,8 @@ namespace rad {
 // Both rings are tile-major: element (tile, slot, c, p) of particle column
 // col = 8 tile + p sits at ((tile * ring + slot) * comps + c) * 8 + p, so the
 // chunk of consecutive slots the kernels stage is one contiguous block.
-// comps is 10, or 11 when sample selectors are defined (the flags word).
+// comps is 10, or 11 when sample selectors are defined (the flags word); the
+// precise-phase FP32 path adds dr's lo part as components 11-13 (comps 14).
 // FP32 split path: slab[tile][slot][c][p] float, c = 0..9 (10) =
 //   dr (3)   : r_m - r_a, the offset from the block's FP64 anchor position
 //   beta (3) : beta_m
@@ -31,6 +32,7 @@ namespace rad {
 // beta (3), bdot (3), g (1), flags (1).
 constexpr int kComps = 11;     // components at most (10 + the selector flags)
 constexpr int kCompsPlain = 10;   // without selectors
+constexpr int kCompsPrec = 14;    // precise-phase FP32 ring: + flags + the lo part of dr
 constexpr int kTileP = 8;      // particles per tile: one warp each
 constexpr int kChunk32 = 32;   // samples per TMA chunk, FP32 ring
 constexpr int kChunk64 = 16;   // samples per TMA chunk, FP64 ring
@@ -315,11 +317,14 @@ struct Accum32Config {
     bool coh;
     int mb;
     bool band = false;   // items with anchor blocks of K << kmul (8 SFU frequencies per thread)
+    bool prec = false;   // float-float offset phase reduced to one turn (8 SFU frequencies)
 };
 bool accum32_ft8_sfu(const Accum32Params* p, const Accum32Config& cfg, int grid,
                      cudaStream_t st, cudaError_t* err, int* nb);
 bool accum32_band(const Accum32Params* p, const Accum32Config& cfg, int grid,
                   cudaStream_t st, cudaError_t* err, int* nb);
+bool accum32_precise(const Accum32Params* p, const Accum32Config& cfg, int grid,
+                     cudaStream_t st, cudaError_t* err, int* nb);
 bool accum32_ft8_mix(const Accum32Params* p, const Accum32Config& cfg, int grid,
                      cudaStream_t st, cudaError_t* err, int* nb);
 bool accum32_ft16(const Accum32Params* p, const Accum32Config& cfg, int grid,

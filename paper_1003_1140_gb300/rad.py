@@ -33,6 +33,7 @@ RAD_FP32_SPLIT = 1
 RAD_VARIANT_AUTO = 0
 RAD_VARIANT_SFU = 1
 RAD_VARIANT_MIX = 2
+RAD_VARIANT_PRECISE = 3
 
 _ERRNAMES = {RAD_EINVAL: "RAD_EINVAL", RAD_ENOMEM: "RAD_ENOMEM", RAD_ECUDA: "RAD_ECUDA",
              RAD_ESTEP: "RAD_ESTEP", RAD_EINCOMPLETE: "RAD_EINCOMPLETE",

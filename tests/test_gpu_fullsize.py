@@ -9,6 +9,9 @@
   1 - n.beta ~ 1/(2 gamma^2) makes the head-on directions sensitive to
   cancellation) with all 4096 samples, 8 directions and 1024 omega on 256
   particles, both precisions against the oracle.
+* The precision workload's upper decade on 65,536 particles, bin by bin, by default,
+  under a phase budget (anchor interval per frequency band) and with the precise
+  phase, against the FP64 path.
 * The batched workload's full structure (electrons + ions, 192 HEALPix
   directions, three grids of 512/1024/2048 omega, five uneven windows of
   512 to 4096 steps) fed one step per call through the per-step CUDA graphs
@@ -98,6 +101,42 @@ def test_gamma10_all_samples():
         for d in range(len(w.dirs)):
             e = np.linalg.norm(S[d] - ref[d]) / np.linalg.norm(ref[d])
             assert e <= tol, (prec, opts, d, e)
+
+
+def test_gamma10_upper_decade_bins():
+    """65,536 electrons of the precision workload (gamma = 10), all 4096 samples, 8
+    directions, 1024 omega, against the FP64 GPU path bin by bin: the FP32 split path
+    by default (anchor blocks of 32 samples), under a 2.1e-5-rad phase budget (blocks
+    of 8 samples for the upper decade's frequency tile, 32 below) and with the precise
+    phase.  Every spectrum within 1e-6 relative L2; in the upper decade the budget at
+    least halves the default's worst bin, and the precise phase keeps every bin within
+    1e-5."""
+    import paper_1003_1140_gb300 as R
+    from trajgen import gpu as tg
+    w = trajgen.config(3, 65536 / 1048576)
+    X, U = tg.trajectory_gpu(w)
+    sp = [(w.n_total, -1.0, 1.0)]
+    S = {}
+    for name, prec, opts in (("fp64", R.RAD_FP64, None), ("default", R.RAD_FP32_SPLIT, None),
+                             ("budget", R.RAD_FP32_SPLIT, {"phase_budget": 2.1e-5}),
+                             ("precise", R.RAD_FP32_SPLIT, {"variant": R.RAD_VARIANT_PRECISE})):
+        with R.Radiation(w.dirs, w.grids, w.dt, sp, w.windows, precision=prec, box_L=w.L,
+                         options=opts) as r:
+            r.accumulate_steps(0, X, U)
+            S[name] = r.finalize()[0]
+            if name == "budget":
+                assert r.options()["anchor_K"] == 8
+    up = w.grids[0] >= 100.0
+    assert up.sum() == 256
+    ref = S["fp64"]
+    worst = {}
+    for name in ("default", "budget", "precise"):
+        worst[name] = (np.abs(S[name] - ref) / ref)[:, up].max()
+        rel = np.linalg.norm(S[name] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        print(f"{name}: upper-decade worst bin {worst[name]:.2e}, rel-L2 {rel.max():.2e}")
+        assert rel.max() <= 1e-6
+    assert worst["budget"] <= 0.6 * worst["default"]
+    assert worst["precise"] <= 1e-5
 
 
 def test_batched_workload4_full_structure_per_step_graphs():

@@ -97,11 +97,11 @@ def test_fp32_split_matches_oracle(two_species, coherent, K):
 
 
 @pytest.mark.parametrize("variant,ft,mb", [(1, 16, 2), (1, 8, 3), (2, 8, 2), (2, 8, 3),
-                                           (2, 16, 2), (1, 4, 4)])
+                                           (2, 16, 2), (1, 4, 4), (3, 8, 2), (3, 8, 3)])
 @pytest.mark.parametrize("coherent", [False, True])
 def test_fp32_split_kernel_variants(two_species, variant, ft, mb, coherent):
-    """SFU-only and SFU + FMA-polynomial (MIX) kernels, 4, 8 or 16 frequencies per
-    thread, built for 2, 3 or 4 resident blocks per SM."""
+    """SFU-only, SFU + FMA-polynomial (MIX) and precise-phase kernels, 4, 8 or 16
+    frequencies per thread, built for 2, 3 or 4 resident blocks per SM."""
     R = _rad()
     w, X, U, ref = two_species
     got = _run(w, X, U, R.RAD_FP32_SPLIT, coherent,
@@ -314,9 +314,9 @@ def test_particle_shards_combine_to_the_whole(two_species, precision, coherent):
     np.testing.assert_allclose(S, whole, rtol=1e-9, atol=1e-12 * np.abs(whole).max())
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision,opts", [(0, None), (1, None), (1, {"variant": 3})])
 @pytest.mark.parametrize("coherent", [False, True])
-def test_selectors_match_oracle(two_species, precision, coherent):
+def test_selectors_match_oracle(two_species, precision, opts, coherent):
     """Windows restricted to a spatial box and to a momentum pitch cone about the
     streaming axis (and one unrestricted window) against the oracle."""
     R = _rad()
@@ -331,16 +331,16 @@ def test_selectors_match_oracle(two_species, precision, coherent):
                          coherent=coherent, box_L=w.L, selectors=sels, window_selector=wsel)
     with R.Radiation(w.dirs, w.grids, w.dt, sp, wins,
                      mode=R.RAD_COHERENT if coherent else R.RAD_INCOHERENT,
-                     precision=precision, box_L=w.L) as r:
+                     precision=precision, box_L=w.L, options=opts) as r:
         r.set_selectors(sels, wsel)
         r.accumulate_steps(0, torch.as_tensor(X, device="cuda"), torch.as_tensor(U, device="cuda"))
         got = r.finalize()
     _check(got, ref, 1e-10 if precision == 0 else 1e-4, per_direction=True)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision,opts", [(0, {}), (1, {}), (1, {"variant": 3})])
 @pytest.mark.parametrize("coherent", [False, True])
-def test_subcycling_matches_oracle(two_species, precision, coherent):
+def test_subcycling_matches_oracle(two_species, precision, opts, coherent):
     """Sub-cycling (4 sub-samples per PIC sample) with a selector, several windows
     and both species, against the oracle's sub-cycled sum."""
     R = _rad()
@@ -353,7 +353,7 @@ def test_subcycling_matches_oracle(two_species, precision, coherent):
                          subcycle=4)
     with R.Radiation(w.dirs, w.grids, w.dt, sp, w.windows,
                      mode=R.RAD_COHERENT if coherent else R.RAD_INCOHERENT,
-                     precision=precision, box_L=w.L, options={"subcycle": 4}) as r:
+                     precision=precision, box_L=w.L, options=dict(opts, subcycle=4)) as r:
         r.set_selectors(sels, wsel)
         r.accumulate_steps(0, torch.as_tensor(X, device="cuda"), torch.as_tensor(U, device="cuda"))
         got = r.finalize()
