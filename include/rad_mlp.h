@@ -76,6 +76,14 @@ int rad_mlp_predict(rad_mlp *m, int32_t batch, const float *x, float *y);
  * BF16 copies of W and W^T refreshed).  Stream ordered; does not wait. */
 int rad_mlp_adam(rad_mlp *m, float lr, float beta1, float beta2, float eps);
 
+/* One training step: rad_mlp_gradients followed by rad_mlp_adam in one call,
+ * with no host synchronisation between the backward pass and the optimiser
+ * (the gradients are stored as by rad_mlp_gradients).  Same arguments and
+ * checks as the two calls; *loss (host, may be NULL) gets the MSE before the
+ * update.  Waits for the stream. */
+int rad_mlp_train_step(rad_mlp *m, int32_t batch, const float *x, const float *t, float lr,
+                       float beta1, float beta2, float eps, double *loss);
+
 /* The tensor-core GEMM on its own: C [M][N] (FP32, device) = op(A) op(B), BF16
  * device operands (16-byte aligned); a_kcontig != 0: A stored [M][K], else
  * [K][M]; b_kcontig != 0: B stored [N][K], else [K][N] (operands stored K-last are first

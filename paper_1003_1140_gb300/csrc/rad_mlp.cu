@@ -984,9 +984,9 @@ int rad_mlp_predict(rad_mlp* m, int32_t batch, const float* x, float* y)
     return gemm_timed_out() ? RAD_MLP_ETIMEOUT : RAD_MLP_OK;
 }
 
-int rad_mlp_gradients(rad_mlp* m, int32_t batch, const float* x, const float* t, double* loss)
+// Forward, MSE and backward, enqueued on the stream (no host synchronisation).
+static int backward(rad_mlp* m, int32_t batch, const float* x, const float* t)
 {
-    if (!m || batch < 1 || batch > m->max_rows || !x || !t) return RAD_MLP_EINVAL;
     const int R = round128(batch);
     int rc = forward(m, batch, x);
     if (rc) return rc;
@@ -1033,15 +1033,26 @@ int rad_mlp_gradients(rad_mlp* m, int32_t batch, const float* x, const float* t,
         column_sums<<<grid_for(m->w[l + 1]), 256, 0, m->st>>>(m->z[l + 1], m->db[l], R, m->w[l + 1]);
         MCU(cudaGetLastError());
     }
+    return RAD_MLP_OK;
+}
+
+static int finish(rad_mlp* m, double* loss)
+{
     if (loss) MCU(cudaMemcpyAsync(loss, m->loss, sizeof(double), cudaMemcpyDeviceToHost, m->st));
     MCU(cudaStreamSynchronize(m->st));
     return gemm_timed_out() ? RAD_MLP_ETIMEOUT : RAD_MLP_OK;
 }
 
-int rad_mlp_adam(rad_mlp* m, float lr, float beta1, float beta2, float eps)
+int rad_mlp_gradients(rad_mlp* m, int32_t batch, const float* x, const float* t, double* loss)
 {
-    if (!m || !(lr > 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f))
-        return RAD_MLP_EINVAL;
+    if (!m || batch < 1 || batch > m->max_rows || !x || !t) return RAD_MLP_EINVAL;
+    const int rc = backward(m, batch, x, t);
+    return rc ? rc : finish(m, loss);
+}
+
+// One Adam step of every layer from the stored gradients, enqueued.
+static int adam_enqueue(rad_mlp* m, float lr, float beta1, float beta2, float eps)
+{
     m->step += 1;
     const float c1 = 1.0f - std::pow(beta1, (float)m->step);
     const float c2 = 1.0f - std::pow(beta2, (float)m->step);
@@ -1056,6 +1067,27 @@ int rad_mlp_adam(rad_mlp* m, float lr, float beta1, float beta2, float eps)
         MCU(cudaGetLastError());
     }
     return RAD_MLP_OK;
+}
+
+static bool adam_args_ok(float lr, float beta1, float beta2)
+{
+    return lr > 0.0f && beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f;
+}
+
+int rad_mlp_adam(rad_mlp* m, float lr, float beta1, float beta2, float eps)
+{
+    if (!m || !adam_args_ok(lr, beta1, beta2)) return RAD_MLP_EINVAL;
+    return adam_enqueue(m, lr, beta1, beta2, eps);
+}
+
+int rad_mlp_train_step(rad_mlp* m, int32_t batch, const float* x, const float* t, float lr,
+                       float beta1, float beta2, float eps, double* loss)
+{
+    if (!m || batch < 1 || batch > m->max_rows || !x || !t || !adam_args_ok(lr, beta1, beta2))
+        return RAD_MLP_EINVAL;
+    int rc = backward(m, batch, x, t);
+    if (!rc) rc = adam_enqueue(m, lr, beta1, beta2, eps);
+    return rc ? rc : finish(m, loss);
 }
 
 int rad_mlp_gemm(int32_t a_kcontig, int32_t b_kcontig, int32_t M, int32_t N, int32_t K, const void* A,

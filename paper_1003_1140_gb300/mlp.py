@@ -9,7 +9,8 @@ from . import rad as _rad
 
 RAD_MLP_OK = 0
 EXPORTED = ("rad_mlp_init", "rad_mlp_set_layer", "rad_mlp_get_layer", "rad_mlp_forward",
-            "rad_mlp_gradients", "rad_mlp_adam", "rad_mlp_gemm", "rad_mlp_check",
+            "rad_mlp_gradients", "rad_mlp_adam", "rad_mlp_train_step", "rad_mlp_gemm",
+            "rad_mlp_check",
             "rad_mlp_set_transform", "rad_mlp_predict",
             "rad_mlp_last_error", "rad_mlp_destroy")
 
@@ -33,6 +34,10 @@ def _lib():
         lib.rad_mlp_adam.restype = ctypes.c_int
         lib.rad_mlp_adam.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                      ctypes.c_float]
+        lib.rad_mlp_train_step.restype = ctypes.c_int
+        lib.rad_mlp_train_step.argtypes = [vp, ctypes.c_int32, vp, vp, ctypes.c_float,
+                                           ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                           ctypes.POINTER(ctypes.c_double)]
         lib.rad_mlp_gemm.restype = ctypes.c_int
         lib.rad_mlp_gemm.argtypes = [ctypes.c_int32] * 5 + [vp, vp, vp]
         lib.rad_mlp_set_transform.restype = ctypes.c_int
@@ -129,10 +134,12 @@ class MLP:
     def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         self._chk(self._lib.rad_mlp_adam(self.h, lr, beta1, beta2, eps), "rad_mlp_adam")
 
-    def train_step(self, x, t, lr):
-        loss = self.gradients(x, t)
-        self.adam(lr)
-        return loss
+    def train_step(self, x, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        """Gradients and Adam in one call (rad_mlp_train_step)."""
+        loss = ctypes.c_double()
+        self._chk(self._lib.rad_mlp_train_step(self.h, x.shape[0], _p(x), _p(t), lr, beta1, beta2,
+                                               eps, ctypes.byref(loss)), "rad_mlp_train_step")
+        return loss.value
 
     def close(self):
         if getattr(self, "h", None):

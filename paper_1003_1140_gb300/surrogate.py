@@ -269,19 +269,26 @@ def gemm_bench(batch=128, reps=20):
     net.init_params(0)
     x = torch.randn((batch, widths[0]), device="cuda")
     t = torch.randn((batch, widths[-1]), device="cuda")
-    for _ in range(3):
-        net.train_step(x, t, 1e-4)
-    torch.cuda.synchronize()
-    e0, e1 = ev(), ev()
-    e0.record()
-    for _ in range(reps):
-        net.train_step(x, t, 1e-4)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
     flop = sum(2.0 * batch * widths[l] * widths[l + 1] for l in range(len(widths) - 1))
-    res["train_step"] = {"batch": batch, "ms": ms,
-                         "gemm_tflops": (3 * flop - 2.0 * batch * widths[0] * widths[1]) / (ms * 1e-3) / 1e12}
+
+    def two_calls(x, t, lr):
+        net.gradients(x, t)
+        net.adam(lr)
+
+    # one call per step, then the same step as gradients + Adam in two calls
+    for name, fn in (("train_step", net.train_step), ("train_step_two_calls", two_calls)):
+        for _ in range(3):
+            fn(x, t, 1e-4)
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record()
+        for _ in range(reps):
+            fn(x, t, 1e-4)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"batch": batch, "ms": ms,
+                     "gemm_tflops": (3 * flop - 2.0 * batch * widths[0] * widths[1]) / (ms * 1e-3) / 1e12}
     net.close()
     return res
 
