@@ -549,6 +549,58 @@ def test_subsample_positions_follow_the_exact_path(uy):
     np.testing.assert_allclose(bd[:, :, 0], bdot, rtol=0, atol=1e-13)
 
 
+def _circle_history(u0, omega, dt, nc):
+    """Leapfrog states of uniform circular motion, u(t) = u0 (cos wt, sin wt, 0)
+    (a uniform magnetic field), and its exact arc r(t) = (u0 / (gamma w)) (sin wt,
+    1 - cos wt, 0)."""
+    g = math.sqrt(1.0 + u0 * u0)
+
+    def pos(t):
+        return np.stack([u0 / (g * omega) * np.sin(omega * t),
+                         u0 / (g * omega) * (1.0 - np.cos(omega * t)), np.zeros_like(t)])
+
+    s = np.arange(nc) * dt
+    th = omega * (s - 0.5 * dt)
+    X = pos(s).T[:, :, None].copy()
+    U = np.zeros((nc, 3, 1))
+    U[:, 0, 0] = u0 * np.cos(th)                           # u_{s-1/2}
+    U[:, 1, 0] = u0 * np.sin(th)
+    return X, U, pos
+
+
+def test_subsample_positions_on_a_circle():
+    """Sec. 2.2 sub-cycling on a uniform circle (u turns at constant |u|).  (a) The
+    sub-sample positions are r_m plus the integral of beta along the linearly
+    interpolated u, here checked against adaptive quadrature of that integral (not
+    Simpson's rule) to 1e-8: Simpson's error h^5 max|beta^(4)| / 2880 is ~1e-9 for
+    this tight turn (|du/dt| = 3), a trapezoid rule's ~1e-5.  (b) They converge to
+    the exact circular arc: halving dt divides the largest distance from the arc by
+    at least 3.5 (8 measured: the interpolated u is second-order accurate and each
+    sub-step integrates it over a fraction of dt)."""
+    from scipy.integrate import quad
+    u0, omega, n = 2.0, 1.5, 4
+    err = []
+    for dt in (0.1, 0.05):
+        nc = int(round(0.6 / dt)) + 1
+        X, U, pos = _circle_history(u0, omega, dt, nc)
+        r, _, _ = oracle.subsamples(X, U, dt, 0.0, n)
+        tau = (np.arange(n) + 0.5) / n - 0.5
+        if dt == 0.1:
+            for m in range(nc - 1):
+                um, up = U[m, :, 0], U[m + 1, :, 0]
+                ub, du = 0.5 * (um + up), up - um
+                for k in range(n):
+                    for c in range(2):
+                        def bc(s, c=c):
+                            uu = ub + (s / dt) * du
+                            return uu[c] / math.sqrt(1.0 + uu @ uu)
+                        q, _ = quad(bc, 0.0, tau[k] * dt, epsabs=1e-14, epsrel=1e-14)
+                        assert abs(r[m * n + k, c, 0] - (X[m, c, 0] + q)) < 1e-8, (m, k, c)
+        t = ((np.arange(nc - 1)[:, None] + tau[None, :]) * dt).reshape(-1)
+        err.append(np.abs(r[:, :, 0] - pos(t).T).max())
+    assert err[0] / err[1] >= 3.5, err
+
+
 def test_subsample_position_pin_catches_a_trapezoid_rule():
     """The 1e-10 bound above is tight enough: the same sub-sample positions by a
     trapezoid rule over [0, tau] (weights 1/2, 1/2), or by Simpson's rule with the
