@@ -589,6 +589,19 @@ def main():
             "worst_bin_vs_fp64": float((np.abs(Sp - S64) / S64).max()),
             "rel_l2_max": float((np.linalg.norm(Sp - S64, axis=1) / np.linalg.norm(S64, axis=1)).max()),
             "kernel_rate": upd64 / (tp["accum_ms"] * 1e-3) / 1e9}
+        # the precise phase only where the phase budget needs it (the upper decade)
+        cq = R.Radiation(w.dirs, w.grids, w.dt, [(n64, q, mass)], w.windows,
+                         precision=R.RAD_FP32_SPLIT, box_L=w.L,
+                         options={"variant": R.RAD_VARIANT_PRECISE, "phase_budget": PHASE_BUDGET})
+        cq.accumulate_steps(0, X64, U64)
+        Sq = cq.finalize()[0]
+        tq = cq.timing()
+        cq.close()
+        perbin["precise_phase_with_budget"] = {
+            "budget_rad": PHASE_BUDGET,
+            "upper_decade_worst_bin_vs_fp64": float((np.abs(Sq - S64) / S64)[:, hi].max()),
+            "rel_l2_max": float((np.linalg.norm(Sq - S64, axis=1) / np.linalg.norm(S64, axis=1)).max()),
+            "kernel_rate": upd64 / (tq["accum_ms"] * 1e-3) / 1e9}
         fp64_rate = upd64 / (t64["accum_ms"] * 1e-3) / 1e9
         fp64 = {"value": fp64_rate, "unit": UNIT,
                 "sample": f"first {n64} particles, same samples/dirs/omegas"}

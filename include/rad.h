@@ -86,7 +86,10 @@ extern "C" {
 #define RAD_VARIANT_PRECISE 3 /* the offset phase nu dphi in float-float, reduced to one
                                  turn before the special-function unit: per-update phase
                                  error ~5e-7 rad instead of ~1e-7 |omega dphi|; 8
-                                 frequencies per thread, anchor interval 32          */
+                                 frequencies per thread, anchor interval 32.  With a
+                                 phase budget (reserved[3]) only the frequency tiles
+                                 whose K = 32 rounding bound w_max 31 dt 2^-24 exceeds
+                                 it take the precise phase, the others the SFU path */
 
 typedef struct rad_ctx rad_ctx;
 

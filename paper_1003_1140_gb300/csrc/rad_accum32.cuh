@@ -123,9 +123,9 @@ struct ChunkMeta {
 };
 constexpr int kFirstOfTile = 1, kLastOfTile = 2, kFirstOfItem = 4, kLastOfItem = 8;
 
-template <int FT, int K, bool COH, bool PREC = false>
+template <int FT, int K, bool COH, int PM = 0>
 struct Smem32 {
-    float tbuf[2][kChunk32][PREC ? kCompsPrec : kComps][kTileP];   // bulk-copy destinations
+    float tbuf[2][kChunk32][PM ? kCompsPrec : kComps][kTileP];     // bulk-copy destinations
                                                       // (producer only; a chunk fills comps rows)
     float tanc[2][kChunk32 / K][6][kTileP];           // the chunk's anchor positions (hi, lo)
     float4 geo[2][kComputeWarps][kChunk32 + 1];       // V1, V2, dphi per particle and sample
@@ -157,10 +157,10 @@ __device__ __forceinline__ void compute_sync(uint64_t* bar, uint32_t& phase, int
     ++phase;
 }
 
-template <int FT, int NP, int K, bool COH, bool PREC = false>
+template <int FT, int NP, int K, bool COH, int PM = 0>
 constexpr size_t smem32_bytes()
 {
-    return sizeof(Smem32<FT, K, COH, PREC>) + 128;
+    return sizeof(Smem32<FT, K, COH, PM>) + 128;
 }
 
 // The producer's walk over (item, tile, chunk): items come from an atomic
@@ -197,14 +197,15 @@ struct ChunkCursor {
 
 // BAND: the work items may take anchor blocks of K << kmul samples (a separate
 // build, so that the common build keeps its blocks at the compile-time K).
-// PREC: the offset phase nu * dphi in float-float, reduced to one turn before
-// the special-function unit (the precise-phase variant).
-template <int FT, int NP, int K, bool COH, int MB, bool BAND = false, bool PREC = false>
+// PM: the precise offset phase (nu * dphi in float-float, reduced to one turn
+// before the special-function unit) for no item (0), every item (1) or the
+// items that ask for it (2); 1 and 2 read a ring that carries dr's lo part.
+template <int FT, int NP, int K, bool COH, int MB, bool BAND = false, int PM = 0>
 __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum32Params p)
 {
     static_assert(NP >= 0 && NP < FT, "polynomial frequencies per thread");
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    auto& S = *reinterpret_cast<Smem32<FT, K, COH, PREC>*>(
+    auto& S = *reinterpret_cast<Smem32<FT, K, COH, PM>*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     // one chunk of the ring: 32 samples x comps components x 8 particles
     const int cstride = p.comps * kTileP;
@@ -449,13 +450,13 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
                 for (int q = 0; q < 3; ++q) {
                     const ff d = two_prod(nh[q], dr[q]);
                     float dl = fmaf(nlo[q], dr[q], d.lo);
-                    if (PREC) dl = fmaf(nh[q], tb[(11 + q) * kTileP], dl);   // n . dr_lo
+                    if (PM) dl = fmaf(nh[q], tb[(11 + q) * kTileP], dl);   // n . dr_lo
                     const ff u = two_sum(sh, -d.hi);
                     sh = u.hi;
                     e = e + (u.lo - dl);
                 }
                 const float dh = sh + e;
-                S.geo[buf][pp][sm] = make_float4(V1, V2, dh, PREC ? e - (dh - sh) : 0.0f);
+                S.geo[buf][pp][sm] = make_float4(V1, V2, dh, PM ? e - (dh - sh) : 0.0f);
             }
             __syncwarp();
             // the item's frequencies (nu hi, lo) for the compute warps, which turn
@@ -504,11 +505,12 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
     }
 
     // ---------------------------------------------------------------- compute
-    float om[FT];   // omega (SFU), omega / 2 (polynomial) or nu_hi = omega / 2 pi (PREC)
-    float nlo[FT];  // PREC: nu_lo
+    float om[FT];   // omega (SFU), omega / 2 (polynomial) or nu_hi = omega / 2 pi (precise)
+    float nlo[FT];  // precise: nu_lo
     float a1r[FT], a1i[FT], a2r[FT], a2i[FT], th[FT];
 #pragma unroll
     for (int i = 0; i < FT; ++i) om[i] = nlo[i] = a1r[i] = a1i[i] = a2r[i] = a2i[i] = th[i] = 0.0f;
+    bool iprec = PM == 1;   // the current item's phases are precise
     uint32_t cphase = 0;
     for (uint32_t L = 0;; ++L) {
         const int buf = L & 1;
@@ -521,10 +523,11 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
         if (flags & kFirstOfItem) {
             const WorkItem it = p.items[ii];
             const WinDev w = p.wins[it.win];
+            if (PM == 2) iprec = it.prec != 0;
 #pragma unroll
             for (int i = 0; i < FT; ++i) {
                 const int k = it.ftile * (32 * FT) + lane + 32 * i;
-                if (PREC) {
+                if (PM != 0 && (PM == 1 || iprec)) {
                     om[i] = (k < w.grid_len) ? p.nu_hi[w.grid_off + k] : 0.0f;
                     nlo[i] = (k < w.grid_len) ? p.nu_lo[w.grid_off + k] : 0.0f;
                 } else {
@@ -538,14 +541,16 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
             for (int i = 0; i < FT; ++i) a1r[i] = a1i[i] = a2r[i] = a2i[i] = 0.0f;
         }
         // update loop, one anchor block at a time; the next sample's geometry
-        // is loaded while the current one is accumulated
+        // is loaded while the current one is accumulated.  P: precise phase (a
+        // compile-time constant unless the build chooses it per item)
+        const bool P = PM == 1 || (PM == 2 && iprec);
 #pragma unroll 1
         for (int b = lo >> ks; (b << ks) < hi; ++b) {
             const int l0 = lo > (b << ks) ? lo : (b << ks);
             const int l1 = hi < ((b + 1) << ks) ? hi : ((b + 1) << ks);
-            // anchor phases Theta_k = 2 pi frac(nu_k phi_ref): float-float
-            // product, exact reduction to one turn; halved for the polynomial
-            // frequencies
+            // anchor phases Theta_k = frac(nu_k phi_ref) turns: float-float
+            // product, exact reduction to one turn; in radians (halved for
+            // the polynomial frequencies) unless the phase is precise
             const float2 an = S.anc[buf][warp][b];
 #pragma unroll
             for (int j = 0; j < FT / 4; ++j) {
@@ -555,9 +560,9 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int i = 4 * j + q;
-                    th[i] = PREC ? anchor_turns(nh[q], nl[q], an)
-                                 : anchor_turns(nh[q], nl[q], an) *
-                                       (i < NS ? 6.28318530717958647f : 3.14159265358979323f);
+                    th[i] = P ? anchor_turns(nh[q], nl[q], an)
+                              : anchor_turns(nh[q], nl[q], an) *
+                                    (i < NS ? 6.28318530717958647f : 3.14159265358979323f);
                 }
             }
             float4 gg = S.geo[buf][warp][l0];
@@ -567,7 +572,7 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
 #pragma unroll
                 for (int i = 0; i < NS; ++i) {
                     float tt;
-                    if (PREC) {
+                    if (P) {
                         // turns: nu dphi = p + (p's rounding error) + nu_lo dphi_hi
                         // + nu_hi dphi_lo (+ Theta); p's integer part removed exactly
                         const float pr = __fmul_rn(om[i], gg.z);
@@ -673,11 +678,11 @@ __global__ void __launch_bounds__(kBlockThreads, MB) accum32_kernel(const Accum3
     }
 }
 
-template <int FT, int NP, int K, bool COH, int MB, bool BAND = false, bool PREC = false>
+template <int FT, int NP, int K, bool COH, int MB, bool BAND = false, int PM = 0>
 cudaError_t launch32_one(const Accum32Params& p, int grid, cudaStream_t st)
 {
-    auto kern = accum32_kernel<FT, NP, K, COH, MB, BAND, PREC>;
-    const size_t smem = smem32_bytes<FT, NP, K, COH, PREC>();
+    auto kern = accum32_kernel<FT, NP, K, COH, MB, BAND, PM>;
+    const size_t smem = smem32_bytes<FT, NP, K, COH, PM>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -685,14 +690,14 @@ cudaError_t launch32_one(const Accum32Params& p, int grid, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template <int FT, int NP, int K, bool COH, int MB, bool BAND = false, bool PREC = false>
+template <int FT, int NP, int K, bool COH, int MB, bool BAND = false, int PM = 0>
 int blocks32_one()
 {
     int nb = 0;
-    const size_t smem = smem32_bytes<FT, NP, K, COH, PREC>();
-    if (cudaFuncSetAttribute(accum32_kernel<FT, NP, K, COH, MB, BAND, PREC>,
+    const size_t smem = smem32_bytes<FT, NP, K, COH, PM>();
+    if (cudaFuncSetAttribute(accum32_kernel<FT, NP, K, COH, MB, BAND, PM>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, accum32_kernel<FT, NP, K, COH, MB, BAND, PREC>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, accum32_kernel<FT, NP, K, COH, MB, BAND, PM>,
                                                       kBlockThreads, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;

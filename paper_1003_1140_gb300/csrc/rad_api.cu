@@ -273,7 +273,7 @@ static void basis(const double n[3], double e1[3], double e2[3])
 bool rad::accum32_dispatch(const Accum32Params* p, const Accum32Config& cfg, int grid,
                            cudaStream_t st, cudaError_t* err, int* nb)
 {
-    if (cfg.prec) return accum32_precise(p, cfg, grid, st, err, nb);
+    if (cfg.pm) return accum32_precise(p, cfg, grid, st, err, nb);
     if (cfg.band) return accum32_band(p, cfg, grid, st, err, nb);
     return accum32_ft8_sfu(p, cfg, grid, st, err, nb) || accum32_ft8_mix(p, cfg, grid, st, err, nb) ||
            accum32_ft16(p, cfg, grid, st, err, nb) || accum32_ft4(p, cfg, grid, st, err, nb);
@@ -287,6 +287,7 @@ static int freq_tile(const rad_ctx* c)
 }
 
 static std::vector<std::vector<int>> band_kmul(const rad_ctx* c, int ftl);
+static std::vector<std::vector<int>> precise_tiles(const rad_ctx* c);
 
 // Build the work items of one event (set of windows) and sort them by cost;
 // with `ranges` only the particle tiles [first, second) of each species (the
@@ -317,6 +318,7 @@ static void build_items(rad_ctx* c, Event& ev, int total_blocks,
     const double target_items = 256.0 * std::max(1, total_blocks);
     int G = (int)std::max(1.0, std::floor(units / target_items));
     const std::vector<std::vector<int>> km = band_kmul(c, ftl);
+    const std::vector<std::vector<int>> pt = precise_tiles(c);
     ev.items.clear();
     std::vector<int64_t> cost;
     for (int w : ev.wins) {
@@ -336,7 +338,8 @@ static void build_items(rad_ctx* c, Event& ev, int total_blocks,
                 for (int row = 0; row < (int)wd.size(); ++row)
                     for (int f = 0; f < nft; ++f) {
                         WorkItem it{w, wd[row], f, s, t0, std::min(G, t_end - t0), row,
-                                    km[W.freq_grid][f]};
+                                    km[W.freq_grid][f],
+                                    c->cfg.pm == 2 ? pt[W.freq_grid][f] : 0};
                         ev.items.push_back(it);
                         cost.push_back((int64_t)it.ntiles * nch);
                     }
@@ -453,7 +456,7 @@ static std::string tune_key(const rad_ctx* c, int K)
           << c->win_dirs[w].size() << ",";
     }
     k << "|d" << c->opt.defer << "|n" << std::max(1, c->opt.subcycle) << "|b" << c->cfg.band
-      << "|p" << c->cfg.prec;
+      << "|p" << c->cfg.pm;
     return k.str();
 }
 
@@ -517,6 +520,7 @@ static void tune_slice(const rad_ctx* c, Event& ev, size_t n)
     const int ftl = freq_tile(c);
     const int nft = (c->grid_len[W.freq_grid] + ftl - 1) / ftl;
     const std::vector<std::vector<int>> km = band_kmul(c, ftl);
+    const std::vector<std::vector<int>> pt = precise_tiles(c);
     const std::vector<int32_t>& wd = c->win_dirs[best];
     for (int s = 0; s < c->n_species && ev.items.size() < n; ++s) {
         if (!((W.species_mask >> s) & 1u)) continue;
@@ -524,7 +528,8 @@ static void tune_slice(const rad_ctx* c, Event& ev, size_t n)
         for (int t = 0; t < nt && ev.items.size() < n; ++t)
             for (int row = 0; row < (int)wd.size() && ev.items.size() < n; ++row)
                 for (int f = 0; f < nft && ev.items.size() < n; ++f)
-                    ev.items.push_back(WorkItem{best, wd[row], f, s, t, 1, row, km[W.freq_grid][f]});
+                    ev.items.push_back(WorkItem{best, wd[row], f, s, t, 1, row, km[W.freq_grid][f],
+                                                c->cfg.pm == 2 ? pt[W.freq_grid][f] : 0});
     }
 }
 
@@ -544,7 +549,7 @@ static int autotune32(rad_ctx* c, int K)
     std::vector<Accum32Config> cands = {{8, 0, K, coh, 2}, {8, 0, K, coh, 3}, {8, 1, K, coh, 2},
                                         {8, 1, K, coh, 3}, {8, 2, K, coh, 2}, {4, 0, K, coh, 4}};
     if (c->cfg.band) cands = {{8, 0, K, coh, 2, true}, {8, 0, K, coh, 3, true}};
-    if (c->cfg.prec) cands = {{8, 0, K, coh, 2, false, true}, {8, 0, K, coh, 3, false, true}};
+    if (c->cfg.pm) cands = {{8, 0, K, coh, 2, false, c->cfg.pm}, {8, 0, K, coh, 3, false, c->cfg.pm}};
     // small problems: not worth timing
     if (rad_updates(c) < (int64_t)2e10) {
         c->cfg = cands[0];
@@ -619,13 +624,48 @@ static int autotune32(rad_ctx* c, int K)
     return RAD_OK;
 }
 
+// Per frequency tile (8 frequencies per thread) of each grid, whether the
+// precise-phase variant takes it: every tile, or with a phase budget the tiles
+// whose rounding bound at K = 32, w_max 31 dt 2^-24, exceeds the budget.
+static std::vector<std::vector<int>> precise_tiles(const rad_ctx* c)
+{
+    std::vector<std::vector<int>> pt(c->n_grids);
+    const int ftl = 32 * 8;
+    const double dts = c->dt / std::max(1, c->opt.subcycle);
+    for (int g = 0; g < c->n_grids; ++g) {
+        const int nft = (c->grid_len[g] + ftl - 1) / ftl;
+        pt[g].assign(nft, 1);
+        if (c->opt.reserved[3] <= 0) continue;
+        for (int f = 0; f < nft; ++f) {
+            double wmax = 0.0;
+            for (int k = f * ftl; k < std::min((f + 1) * ftl, c->grid_len[g]); ++k)
+                wmax = std::max(wmax, std::fabs(c->h_freqs[c->grid_off[g] + k]));
+            pt[g][f] = wmax * 31.0 * dts * std::ldexp(1.0, -24) > phase_budget(c);
+        }
+    }
+    return pt;
+}
+
+// The precise-phase build: 0 none, 1 every item, 2 the items of precise tiles.
+static int precise_mode(const rad_ctx* c)
+{
+    if (c->precision != RAD_FP32_SPLIT || c->opt.variant != RAD_VARIANT_PRECISE) return 0;
+    bool any = false, all = true;
+    for (const auto& g : precise_tiles(c))
+        for (int v : g) {
+            any = any || v;
+            all = all && v;
+        }
+    return all ? 1 : (any ? 2 : 0);
+}
+
 // Freeze options: pick K / FT, build events and their item lists.
 static int freeze(rad_ctx* c)
 {
     if (c->frozen) return RAD_OK;
     CU(cudaSetDevice(c->device));
-    if (c->precision == RAD_FP32_SPLIT && c->opt.variant == RAD_VARIANT_PRECISE &&
-        c->comps != kCompsPrec) {
+    const int pm = precise_mode(c);
+    if (pm && c->comps != kCompsPrec) {
         // the precise-phase ring also carries the lo part of each position offset
         CU(cudaFree(c->slab32));
         c->slab32 = nullptr;
@@ -673,16 +713,17 @@ static int freeze(rad_ctx* c)
             return fail(c, RAD_EINVAL, "4 frequencies per thread is built for 4 blocks per SM, SFU only");
         if (c->cfg.ft == 8 && c->cfg.mb == 4)
             return fail(c, RAD_EINVAL, "8 frequencies per thread is built for 2 or 3 blocks per SM");
-        const bool prec = c->opt.variant == RAD_VARIANT_PRECISE;
-        c->cfg.prec = prec;
+        const bool prec = pm != 0;
+        c->cfg.pm = pm;
         if (prec) {
             // one turn of phase per update regardless of K: the ring's anchor
             // interval stays at 32
             c->K = 32;
             c->cfg.K = 32;
         }
-        const bool tune = (c->opt.variant == RAD_VARIANT_AUTO || prec) && !c->opt.freq_per_lane &&
-                          !c->opt.blocks_per_sm;
+        const bool tune = (c->opt.variant == RAD_VARIANT_AUTO ||
+                           c->opt.variant == RAD_VARIANT_PRECISE) &&
+                          !c->opt.freq_per_lane && !c->opt.blocks_per_sm;
         c->per_band_K = false;
         if (!prec && !c->opt.anchor_K && (tune || c->opt.reserved[3] > 0)) {
             c->K = budget_K(c);
@@ -1535,7 +1576,7 @@ int rad_get_options(const rad_ctx* c, rad_options* o)
         o->anchor_K = c->cfg.K;
         o->freq_per_lane = c->cfg.ft;
         o->blocks_per_sm = c->cfg.mb;
-        o->variant = c->cfg.prec ? RAD_VARIANT_PRECISE
+        o->variant = c->cfg.pm ? RAD_VARIANT_PRECISE
                                  : (c->cfg.np > 0 ? RAD_VARIANT_MIX : RAD_VARIANT_SFU);
         o->reserved[1] = c->cfg.np;
     }

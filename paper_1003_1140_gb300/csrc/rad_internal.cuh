@@ -55,6 +55,7 @@ struct WorkItem {
     int32_t ntiles;   // number of particle tiles
     int32_t row;      // output row of the direction in the window's [dirs][len] block
     int32_t kmul;     // FP32 path: phases anchored every K << kmul samples (K: the ring's)
+    int32_t prec;     // FP32 path, precise-phase build for chosen items: 1 = this item
 };
 
 // Per-window constants the accumulation kernels read.
@@ -317,7 +318,8 @@ struct Accum32Config {
     bool coh;
     int mb;
     bool band = false;   // items with anchor blocks of K << kmul (8 SFU frequencies per thread)
-    bool prec = false;   // float-float offset phase reduced to one turn (8 SFU frequencies)
+    int pm = 0;          // precise offset phase (8 SFU frequencies, K 32): 0 none, 1 every
+                         // item, 2 the items whose WorkItem.prec is set
 };
 bool accum32_ft8_sfu(const Accum32Params* p, const Accum32Config& cfg, int grid,
                      cudaStream_t st, cudaError_t* err, int* nb);

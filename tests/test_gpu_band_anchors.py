@@ -15,7 +15,9 @@ K = 32, 16 and 8:
   same arithmetic, up to the order of the FP64 sums);
 * each lower tile is as accurate against the oracle as the uniform context at
   the K it was given -- its blocks combine several ring blocks, with the ring
-  anchors' offsets n . (r_a - r_A) added in float-float, at no loss.
+  anchors' offsets n . (r_a - r_A) added in float-float, at no loss;
+* the precise-phase variant under a budget takes the precise phase only in the
+  tiles that need it.
 """
 import numpy as np
 import pytest
@@ -83,6 +85,41 @@ def test_anchor_interval_per_band(beams):
             db = np.linalg.norm(band[wi][:, s] - uni[K][wi][:, s], axis=1) / \
                 np.linalg.norm(e[:, s], axis=1)
             assert np.all(db <= 2.0 * eu + 1e-7), (wi, t, db, eu)
+
+
+def test_precise_phase_per_band(beams):
+    """The precise-phase variant under a phase budget takes the precise phase only in
+    the frequency tiles whose rounding bound at K = 32, w_max 31 dt 2^-24, exceeds the
+    budget (here the upper two of three).  Those tiles equal the all-precise context's
+    (the same arithmetic, up to the order of the FP64 sums); the lowest tile runs the
+    SFU path and is as accurate against the oracle as the default context."""
+    import paper_1003_1140_gb300 as R
+    w, X, U, grid, wins, ref = beams
+    budget = 3e-6
+    tiles = [slice(256 * t, 256 * t + 256) for t in range(3)]
+    bound = [np.abs(grid[s]).max() * 31 * w.dt * 2.0 ** -24 for s in tiles]
+    assert [b > budget for b in bound] == [False, True, True]
+    base = {"freq_per_lane": 8, "blocks_per_sm": 3}
+    hyb, o = _run(R, w, X, U, grid, wins, dict(base, variant=3, phase_budget=budget))
+    assert o["variant"] == 3 and o["anchor_K"] == 32
+    allp, _ = _run(R, w, X, U, grid, wins, dict(base, variant=3))
+    dflt, _ = _run(R, w, X, U, grid, wins, dict(base, variant=1, anchor_K=32))
+    for wi in range(len(wins)):
+        e = ref[wi]
+        for d in range(e.shape[0]):
+            err = np.linalg.norm(hyb[wi][d] - e[d]) / np.linalg.norm(e[d])
+            assert err <= 1e-4, (wi, d, err)
+        up = slice(256, 768)
+        np.testing.assert_allclose(hyb[wi][:, up], allp[wi][:, up], rtol=1e-9,
+                                   atol=1e-12 * np.abs(e).max())
+        s = tiles[0]
+        eh = np.linalg.norm(hyb[wi][:, s] - e[:, s], axis=1) / np.linalg.norm(e[:, s], axis=1)
+        ed = np.linalg.norm(dflt[wi][:, s] - e[:, s], axis=1) / np.linalg.norm(e[:, s], axis=1)
+        print(f"window {wi} SFU tile: per-band precise {eh.max():.2e}, default {ed.max():.2e}")
+        assert np.all(eh <= 2.0 * ed + 1e-7), (wi, eh, ed)
+    # a budget no tile exceeds leaves the SFU path everywhere
+    _, o0 = _run(R, w, X, U, grid, wins, dict(base, variant=3, phase_budget=1e-4))
+    assert o0["variant"] == 1
 
 
 def test_phase_budget_must_not_be_negative():
