@@ -46,8 +46,8 @@ METRIC = "G particle·step·ω·n updates/s, FP32 split vs FP64 GPU at ≤1e-4 r
 # workload scaled to 4096 particles (same samples, directions and omegas), valid while
 # the code (comments aside) of the kernel and of its work-list builder is the code that
 # was captured; traffic scales with the particle count.
-TRAFFIC_CAPTURE = {"sources_sha256": "cd2a1173eed9cbc6a03edf1df4878c6c029c1032cd9c5c9a00e37bb5fc510f56",
-                   "bytes_per_launch": 699.68512e6, "particles": 4096}
+TRAFFIC_CAPTURE = {"sources_sha256": "cadabcb64484e3e00e449b1f01f7142ba83ff5aac4b20d3cd0e4aa48eb6da180",
+                   "bytes_per_launch": 699.964416e6, "particles": 4096}
 UNIT = "G updates/s"
 # phase budget (rad per update) of the accuracy side-run: the upper decade of the
 # precision workload's grid (dt 0.05, w <= 1000) takes anchor blocks of 8 samples
