@@ -5,8 +5,8 @@ frequency at a few directions (one per HEALPix base pixel for the 192-direction
 grid) -- computed exactly by the radiation library.  A ReLU MLP (BF16 weights,
 FP32 accumulation, trained by the library's own tensor-core kernels) maps the
 normalised log10 sparse spectrum to the normalised log10 dense spectrum.  The
-full accumulation is both the fallback and the judge: held-out spectra are
-compared with it, and with the method without the network (interpolation of
+full accumulation is both the fallback and the measure of its error: held-out
+spectra are compared with it, and with the method without the network (interpolation of
 the sparse set in log-frequency and, across directions, from the nearest
 sparse direction).
 
