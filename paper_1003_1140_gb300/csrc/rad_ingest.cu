@@ -108,6 +108,10 @@ __device__ uint32_t selector_bits(const IngestParams& p, const double x[3], cons
 
 // 64-thread blocks (launch_ingest), at least 8 resident per SM: the FP64-bound
 // loop needs the warps to hide its latency more than it needs registers.
+// PRING: the ring is the precise-phase one (comps >= kCompsPrec), which also
+// takes the lo part of each position offset -- a build of its own, so that the
+// FP64-bound common build carries none of that work.
+template <bool PRING>
 __global__ void __launch_bounds__(64, 8) ingest_kernel(const IngestParams p)
 {
     const int64_t cnt = p.count ? p.count : p.n_in - p.first;
@@ -264,7 +268,7 @@ __global__ void __launch_bounds__(64, 8) ingest_kernel(const IngestParams p)
                         const double d = rk[c] - ra[c];
                         const float dh = (float)d;
                         o[c * kTileP] = dh;
-                        if (p.comps >= kCompsPrec) o[(11 + c) * kTileP] = (float)(d - (double)dh);
+                        if (PRING) o[(11 + c) * kTileP] = (float)(d - (double)dh);
                         o[(3 + c) * kTileP] = (float)bk[c];
                         o[(6 + c) * kTileP] = (float)bd[c];
                     }
@@ -326,7 +330,7 @@ __global__ void __launch_bounds__(64, 8) ingest_kernel(const IngestParams p)
                 const float dh = (float)d;
                 o[c * kTileP] = dh;
                 // precise-phase ring: the rounding of the offset as its lo part
-                if (p.comps >= kCompsPrec) o[(11 + c) * kTileP] = (float)(d - (double)dh);
+                if (PRING) o[(11 + c) * kTileP] = (float)(d - (double)dh);
             }
             o[3 * kTileP] = ub[0] * igb;
             o[4 * kTileP] = ub[1] * igb;
@@ -406,7 +410,11 @@ __global__ void store_state(const IngestParams p)
     }
 }
 
-const void* ingest_kernel_ptr() { return reinterpret_cast<const void*>(&ingest_kernel); }
+IngestKernels ingest_kernel_ptr()
+{
+    return {reinterpret_cast<const void*>(&ingest_kernel<false>),
+            reinterpret_cast<const void*>(&ingest_kernel<true>)};
+}
 
 cudaError_t launch_ingest(const IngestParams& p, cudaStream_t st)
 {
@@ -445,7 +453,10 @@ cudaError_t launch_ingest(const IngestParams& p, cudaStream_t st)
         wind_kernel<<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(q);
     }
     const int64_t blocks = (cnt * q.n_seg + threads - 1) / threads;
-    ingest_kernel<<<(unsigned)blocks, threads, 0, st>>>(q);
+    if (q.slab32 && q.comps >= kCompsPrec)
+        ingest_kernel<true><<<(unsigned)blocks, threads, 0, st>>>(q);
+    else
+        ingest_kernel<false><<<(unsigned)blocks, threads, 0, st>>>(q);
     if (q.n_seg > 1) store_state<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(q);
     return cudaGetLastError();
 }

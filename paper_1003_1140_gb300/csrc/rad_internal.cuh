@@ -303,7 +303,14 @@ struct Accum64Params {
 };
 
 cudaError_t launch_ingest(const IngestParams& p, cudaStream_t st);
-const void* ingest_kernel_ptr();
+// The two builds of the ingest kernel (common ring, precise-phase ring); a
+// kernel function pointer compares equal to the set when it is either build.
+struct IngestKernels {
+    const void* plain;
+    const void* precise;
+};
+inline bool operator==(const void* f, const IngestKernels& k) { return f == k.plain || f == k.precise; }
+IngestKernels ingest_kernel_ptr();
 
 // Stream a radiation context orders its work on (for in-library callers that
 // hand it device buffers from another stream).
