@@ -33,9 +33,15 @@
 //   polynomial -- Cody-Waite reduction of theta/2 by multiples of pi, minimax
 //   sin (degree 9) and cos (degree 8) on [-pi/2, pi/2], double angle -- so
 //   both the MUFU and the FMA pipes carry the transcendental work.
+// * Builds beside the common one: per-item anchor blocks of K << kmul samples
+//   (BAND: longer blocks for lower frequency tiles under a phase budget), and
+//   the precise phase (PM: nu dphi in float-float from a ring that carries the
+//   position offsets' lo parts, reduced to one turn before the special-function
+//   unit; for every item or per item).
 // * The trajectory ring is tile-major ([tile][slot][comp][8 particles]), so a
-//   chunk of 32 samples x 11 components x 8 particles is one contiguous 11 KB
-//   block (its anchor positions another), staged into shared memory by bulk
+//   chunk of 32 samples x 10 components (11 with selector flags, 14 for the
+//   precise phase) x 8 particles is one contiguous block (its anchor positions
+//   another), staged into shared memory by bulk
 //   TMA copies (cp.async.bulk).  Warp specialisation: a producer warp issues
 //   the copies and turns each chunk into geometry and reference phases in
 //   shared memory (double-buffered, mbarrier hand-off); eight compute warps,
